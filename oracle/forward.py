@@ -1,0 +1,87 @@
+"""Time marching of the state and adjoint equations (Eq. 8; Sec. 1 reduced-space steps).
+
+Test infrastructure (see the package header).
+
+forward_march : C^0 = C_0, then for n = 1..M solve
+                (B + theta tau S) C^n = (B - (1-theta) tau S) C^{n-1}
+                                        + tau B ((1-theta) f^{n-1} + theta f^n)
+                with C = 0 on the Dirichlet nodes (p = 0).
+adjoint_march : G^M = 0, then for n = M-1..0 solve
+                (B + theta tau S^T) G^n = (B - (1-theta) tau S^T) G^{n+1}
+                                          - tau B3 ((1-theta) (C^n - Ceps^n)
+                                                    + theta (C^{n+1} - Ceps^{n+1}))
+                with G = 0 on the Dirichlet nodes.
+observations  : C at the sensor nodes with multiplicative noise
+                C^eps = C + eps r C (Sec. 4), r passed in.
+
+The linear solves use scipy's sparse LU (a library routine as one step).
+
+Pins: tests/test_oracle_kkt.py (manufactured-solution convergence orders in
+h and tau; the marched (C, f) pair zeroes the C rows of F_h; the marched
+adjoint zeroes the G rows).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .kkt import Problem
+
+
+def _dirichlet_rows(Mat: sp.csr_matrix, D: np.ndarray) -> sp.csr_matrix:
+    keep = sp.diags((~D).astype(np.float64))
+    return (keep @ Mat + sp.diags(D.astype(np.float64))).tocsc()
+
+
+def forward_march(p: Problem, f: np.ndarray, c0: np.ndarray | None = None,
+                  rhs_extra: np.ndarray | None = None) -> np.ndarray:
+    """State C^0..C^M (shape (M+1, N)) for nodal source values f (shape (M+1, N)).
+
+    rhs_extra[n] (n >= 1), if given, is added to the right-hand side of step n
+    (used by the manufactured-solution tests).
+    """
+    th, tau, D = p.theta, p.tau, p.dirichlet
+    lhs = spla.splu(_dirichlet_rows(p.B + th * tau * p.S, D))
+    R = (p.B - (1.0 - th) * tau * p.S).tocsr()
+    C = np.zeros((p.L, p.N))
+    if c0 is not None:
+        C[0] = c0
+    C[0, D] = 0.0
+    for n in range(1, p.L):
+        r = R @ C[n - 1] + tau * (p.B @ ((1.0 - th) * f[n - 1] + th * f[n]))
+        if rhs_extra is not None:
+            r = r + rhs_extra[n]
+        r[D] = 0.0
+        C[n] = lhs.solve(r)
+    return C
+
+
+def adjoint_march(p: Problem, C: np.ndarray, c_obs: np.ndarray,
+                  rhs_extra: np.ndarray | None = None) -> np.ndarray:
+    """Adjoint G^0..G^M for state C (M+1, N) and observations c_obs (M+1, s)."""
+    th, tau, D = p.theta, p.tau, p.dirichlet
+    St = p.S.T.tocsr()
+    lhs = spla.splu(_dirichlet_rows(p.B + th * tau * St, D))
+    R = (p.B - (1.0 - th) * tau * St).tocsr()
+    s = np.where(D, 0.0, p.s)
+    G = np.zeros((p.L, p.N))
+    for n in range(p.M - 1, -1, -1):
+        mis = np.zeros((2, p.N))
+        for q, m in enumerate((n, n + 1)):
+            obs = np.zeros(p.N)
+            np.add.at(obs, p.sensor_node, c_obs[m])
+            mis[q] = s * C[m] - np.where(D, 0.0, obs)
+        r = R @ G[n + 1] - tau * ((1.0 - th) * mis[0] + th * mis[1])
+        if rhs_extra is not None:
+            r = r + rhs_extra[n]
+        r[D] = 0.0
+        G[n] = lhs.solve(r)
+    return G
+
+
+def observations(p: Problem, C: np.ndarray, r: np.ndarray, eps: float) -> np.ndarray:
+    """C^eps at the sensors, shape (M+1, s): C + eps r C (Sec. 4)."""
+    Cs = C[:, p.sensor_node]
+    return Cs + eps * r * Cs

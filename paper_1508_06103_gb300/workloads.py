@@ -1,0 +1,280 @@
+"""Seeded synthetic inputs for the space-time inverse source problem.
+
+This module only *describes* problems: the grid, the coefficient fields a(x)
+and v(x) sampled at cell centroids, the sensor positions (snapped to nodes),
+the true source f(x, t) used to make observation data, and the standard
+normal draws r of the multiplicative noise model C^eps = C + eps r C
+(Section 4, data generation).  It holds none of the method's arithmetic
+(no discretisation, no solver), so that both the CPU oracle and the CUDA
+path can take their inputs from here without sharing any computation.
+
+Conventions
+-----------
+* Domain [0, lx] x [0, ly] x [0, lz], uniform hexahedral cells
+  ``cells = (cx, cy, cz)``; nodes per axis ``n = c + 1``.
+* Node id ``j = ix + nx * (iy + ny * iz)``; cell id ``e = ex + cx * (ey + cy * ez)``.
+* Time levels ``t^n = n * T / M`` for ``n = 0..M``.
+* ``dirichlet_faces`` is a bit mask of the faces carrying the Dirichlet part
+  Gamma_1 of the boundary: bit 0 x=0, bit 1 x=lx, bit 2 y=0, bit 3 y=ly,
+  bit 4 z=0, bit 5 z=lz.  The other faces form the Neumann part Gamma_2.
+* ``beta`` of a workload maps to (beta1, beta2) = (beta / 100, beta): the
+  ratio the paper uses in its Examples 1 and 2 (Section 4.1).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Sequence, Tuple
+
+import numpy as np
+
+FACE_X0, FACE_X1, FACE_Y0, FACE_Y1, FACE_Z0, FACE_Z1 = 1, 2, 4, 8, 16, 32
+ALL_FACES = 63
+
+
+@dataclasses.dataclass
+class Source:
+    """One Gaussian source amp * exp(-|x - c(t)|^2 / (2 sigma^2)) * w(t)."""
+
+    center: Callable[[float], Tuple[float, float, float]]
+    sigma: float = 0.1
+    amp: float = 1.0
+    switch: Callable[[float], float] = lambda t: 1.0
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    cells: Tuple[int, int, int]
+    lengths: Tuple[float, float, float]
+    T: float
+    M: int
+    theta: float
+    dirichlet_faces: int
+    a_cell: np.ndarray          # (ncell,)   diffusivity at cell centroids
+    v_cell: np.ndarray          # (ncell, 3) velocity at cell centroids
+    sensor_xyz: np.ndarray      # (s, 3)     sensor positions
+    beta1: float
+    beta2: float
+    sources: List[Source]
+    noise_eps: float
+    noise_seed: int
+    # solver settings (paper Section 4 / Table 3 defaults where the workload is silent)
+    nsub: Tuple[int, int, int, int] = (2, 2, 2, 2)
+    overlap: int = 1
+    local: str = "ilu0"
+    coarse_cells: Tuple[int, int, int] | None = None
+    coarse_M: int | None = None
+    coarse_overlap: int = 1
+    coarse_rtol: float = 1e-1
+    coarse_maxit: int = 4
+    restart: int = 30
+    rtol: float = 1e-8
+
+    # ---- derived sizes -------------------------------------------------
+    @property
+    def nodes(self) -> Tuple[int, int, int]:
+        return tuple(c + 1 for c in self.cells)
+
+    @property
+    def N(self) -> int:
+        nx, ny, nz = self.nodes
+        return nx * ny * nz
+
+    @property
+    def P(self) -> int:
+        return self.N * (self.M + 1)
+
+    @property
+    def unknowns(self) -> int:
+        return 3 * self.P
+
+    @property
+    def tau(self) -> float:
+        return self.T / self.M
+
+    @property
+    def h(self) -> Tuple[float, float, float]:
+        return tuple(l / c for l, c in zip(self.lengths, self.cells))
+
+    def node_coords(self) -> np.ndarray:
+        """(N, 3) coordinates of the nodes in node-id order."""
+        nx, ny, nz = self.nodes
+        hx, hy, hz = self.h
+        iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        return np.stack([ix.ravel() * hx, iy.ravel() * hy, iz.ravel() * hz], axis=1)
+
+    def sensor_nodes(self) -> np.ndarray:
+        return snap_to_nodes(self.sensor_xyz, self.cells, self.lengths)
+
+    def noise(self) -> np.ndarray:
+        """Standard normal draws r, shape (M+1, s), one per sensor sample."""
+        rng = np.random.Generator(np.random.PCG64(self.noise_seed))
+        return rng.standard_normal((self.M + 1, len(self.sensor_xyz)))
+
+    def true_source(self) -> np.ndarray:
+        """Nodal values of the true source, shape (M+1, N)."""
+        xyz = self.node_coords()
+        out = np.zeros((self.M + 1, self.N))
+        for n in range(self.M + 1):
+            t = n * self.tau
+            for s in self.sources:
+                c = np.asarray(s.center(t))
+                r2 = ((xyz - c) ** 2).sum(axis=1)
+                out[n] += s.amp * s.switch(t) * np.exp(-r2 / (2.0 * s.sigma ** 2))
+        return out
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def cell_centroids(cells: Sequence[int], lengths: Sequence[float]) -> np.ndarray:
+    cx, cy, cz = cells
+    hx, hy, hz = (l / c for l, c in zip(lengths, cells))
+    ez, ey, ex = np.meshgrid(np.arange(cz), np.arange(cy), np.arange(cx), indexing="ij")
+    return np.stack([(ex.ravel() + 0.5) * hx, (ey.ravel() + 0.5) * hy, (ez.ravel() + 0.5) * hz], axis=1)
+
+
+def snap_to_nodes(xyz: np.ndarray, cells: Sequence[int], lengths: Sequence[float]) -> np.ndarray:
+    """Nearest node of each point; a tie goes to the lower index."""
+    nx, ny, nz = (c + 1 for c in cells)
+    idx = []
+    for d, (c, l) in enumerate(zip(cells, lengths)):
+        u = xyz[:, d] * c / l
+        # round half down: ceil(u - 0.5)
+        k = np.ceil(u - 0.5 - 1e-12).astype(np.int64)
+        idx.append(np.clip(k, 0, c))
+    return (idx[0] + nx * (idx[1] + ny * idx[2])).astype(np.int32)
+
+
+def sensor_lattice(m: int, lengths: Sequence[float]) -> np.ndarray:
+    """m^3 sensors at ((k+1)/(m+1)) * L along each axis."""
+    g = [(np.arange(m) + 1.0) / (m + 1.0) * l for l in lengths]
+    z, y, x = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+def smooth_random_field(xyz: np.ndarray, seed: int, modes: int = 8, kmax: int = 3) -> np.ndarray:
+    """Sum of `modes` seeded Fourier modes (wave numbers <= kmax), min-max scaled to [0, 1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    val = np.zeros(len(xyz))
+    for _ in range(modes):
+        k = rng.integers(0, kmax + 1, size=3)
+        phase = rng.uniform(0.0, 2.0 * math.pi, size=3)
+        amp = rng.uniform(0.5, 1.0)
+        val += amp * np.prod(np.cos(math.pi * k[None, :] * xyz + phase[None, :]), axis=1)
+    lo, hi = val.min(), val.max()
+    return (val - lo) / (hi - lo) if hi > lo else np.zeros_like(val)
+
+
+def circular_path(k: int, K: int, T: float, z: float, radius: float = 0.25):
+    def c(t: float):
+        ang = 2.0 * math.pi * t / T + 2.0 * math.pi * k / K
+        return (0.5 + radius * math.cos(ang), 0.5 + radius * math.sin(ang), z)
+    return c
+
+
+def linear_path(p0, p1, T: float):
+    def c(t: float):
+        s = t / T
+        return tuple(a + s * (b - a) for a, b in zip(p0, p1))
+    return c
+
+
+def switching(windows: Sequence[Tuple[float, float]]):
+    def w(t: float) -> float:
+        return 1.0 if any(a <= t < b for a, b in windows) else 0.0
+    return w
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+
+def tiny(theta: float = 1.0) -> Workload:
+    """8^3 cells x 16 implicit-Euler steps, one source moving on a line, 27 sensors."""
+    cells, L = (8, 8, 8), (1.0, 1.0, 1.0)
+    ncell = 8 ** 3
+    beta = 1e-3
+    return Workload(
+        name="tiny_8x8x8x16", cells=cells, lengths=L, T=1.0, M=16, theta=theta,
+        dirichlet_faces=ALL_FACES,
+        a_cell=np.full(ncell, 0.1), v_cell=np.tile([1.0, 0.5, 0.0], (ncell, 1)),
+        sensor_xyz=sensor_lattice(3, L), beta1=beta / 100, beta2=beta,
+        sources=[Source(center=linear_path((0.3, 0.3, 0.5), (0.7, 0.7, 0.5), 1.0))],
+        noise_eps=0.01, noise_seed=1,
+        nsub=(2, 2, 2, 2), overlap=1, local="lu", restart=30, rtol=1e-8,
+    )
+
+
+def mid(cells=(32, 32, 32), M: int = 64, nsub=(4, 4, 4, 4), overlap: int = 2,
+        coarse_cells=(16, 16, 16), coarse_M: int = 32, name: str | None = None) -> Workload:
+    """32^3 cells x 64 Crank-Nicolson steps, two sources on circles, 125 sensors.
+
+    a = 0.05 + 0.05 rho(x) with rho a seeded smooth field; v = (1, 1, 0) sin(pi z);
+    Dirichlet on x = 0 only; beta = 1e-3 at 32 cells per axis.  Smaller `cells`/`M`
+    give the same problem family at sizes the oracle solves in seconds; there beta
+    is scaled with h^2 so that the ratio of the source-equation diagonal
+    beta2 (grad g, grad g) to the mass coupling (g, g), about 9 beta2 / h^2, stays
+    what it is at 32 cells (the balance that decides how well ILU(0) works).
+    """
+    L = (1.0, 1.0, 1.0)
+    cen = cell_centroids(cells, L)
+    a = 0.05 + 0.05 * smooth_random_field(cen, seed=2)
+    v = np.stack([np.sin(math.pi * cen[:, 2]), np.sin(math.pi * cen[:, 2]), np.zeros(len(cen))], axis=1)
+    beta = 1e-3 * (32.0 / cells[0]) ** 2
+    srcs = [Source(center=circular_path(k, 2, 1.0, z)) for k, z in enumerate((0.6, 0.4))]
+    return Workload(
+        name=name or f"mid_{cells[0]}x{cells[1]}x{cells[2]}x{M}", cells=tuple(cells), lengths=L,
+        T=1.0, M=M, theta=0.5, dirichlet_faces=FACE_X0, a_cell=a, v_cell=v,
+        sensor_xyz=sensor_lattice(5, L), beta1=beta / 100, beta2=beta, sources=srcs,
+        noise_eps=0.01, noise_seed=2, nsub=tuple(nsub), overlap=overlap, local="ilu0",
+        coarse_cells=tuple(coarse_cells) if coarse_cells else None, coarse_M=coarse_M,
+        coarse_overlap=1, coarse_rtol=1e-1, coarse_maxit=4, restart=30, rtol=1e-8,
+    )
+
+
+def large() -> Workload:
+    """64^3 cells x 128 steps, layered a with 100x contrast, rotating v, 3 switching sources."""
+    cells, L = (64, 64, 64), (1.0, 1.0, 1.0)
+    cen = cell_centroids(cells, L)
+    band = np.floor(cen[:, 2] * 8).astype(int)
+    a = np.where(band % 2 == 0, 0.01, 1.0)
+    v = np.stack([-(cen[:, 1] - 0.5), cen[:, 0] - 0.5, np.full(len(cen), 0.2)], axis=1)
+    beta = 1e-3
+    srcs = [
+        Source(center=circular_path(0, 3, 1.0, 0.5), switch=switching([(0.0, 0.4), (0.7, 1.01)])),
+        Source(center=circular_path(1, 3, 1.0, 0.35), switch=switching([(0.2, 0.8)])),
+        Source(center=circular_path(2, 3, 1.0, 0.65), switch=switching([(0.0, 0.3), (0.5, 0.9)])),
+    ]
+    return Workload(
+        name="large_64x64x64x128", cells=cells, lengths=L, T=1.0, M=128, theta=0.5,
+        dirichlet_faces=FACE_X0, a_cell=a, v_cell=v, sensor_xyz=sensor_lattice(8, L),
+        beta1=beta / 100, beta2=beta, sources=srcs, noise_eps=0.02, noise_seed=5,
+        nsub=(8, 8, 8, 8), overlap=2, local="ilu0", coarse_cells=(16, 16, 16), coarse_M=32,
+        coarse_overlap=1, restart=40, rtol=1e-8,
+    )
+
+
+def random_small(seed: int, cells=(5, 4, 3), M: int = 5, theta: float = 0.5,
+                 dirichlet_faces: int = FACE_X0 | FACE_Y1, nsens: int = 6) -> Workload:
+    """Small problem with random coefficients, for parity tests on ragged sizes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = (1.0, 0.8, 0.6)
+    ncell = int(np.prod(cells))
+    a = rng.uniform(0.05, 0.2, ncell)
+    v = rng.uniform(-1.0, 1.0, (ncell, 3))
+    xyz = rng.uniform(0.0, 1.0, (nsens, 3)) * np.asarray(L)
+    return Workload(
+        name=f"random_{seed}", cells=tuple(cells), lengths=L, T=1.0, M=M, theta=theta,
+        dirichlet_faces=dirichlet_faces, a_cell=a, v_cell=v, sensor_xyz=xyz,
+        beta1=1e-4, beta2=1e-2, sources=[Source(center=lambda t: (0.5, 0.4, 0.3))],
+        noise_eps=0.0, noise_seed=seed,
+    )
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    """Seeded standard normal vector."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(n)

@@ -1,0 +1,181 @@
+"""Pins of the oracle's Schwarz preconditioners and Krylov solvers (Sec. 3.2, 4)."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import kkt, krylov, schwarz
+from paper_1508_06103_gb300 import workloads as W
+
+
+def _small(seed=21, cells=(3, 3, 2), M=3, faces=W.FACE_X0):
+    w = W.random_small(seed, cells=cells, M=M, dirichlet_faces=faces, nsens=4)
+    p = kkt.Problem.from_workload(w)
+    return p, kkt.assemble(p)
+
+
+def test_partition_rule():
+    assert schwarz.partition(33, 4) == [(0, 9), (9, 17), (17, 25), (25, 33)]
+    assert schwarz.partition(65, 4) == [(0, 17), (17, 33), (33, 49), (49, 65)]
+    assert schwarz.partition(5, 5) == [(k, k + 1) for k in range(5)]
+
+
+def test_owned_sets_partition_the_unknowns():
+    p, F = _small()
+    owner = np.zeros(p.n, dtype=int)
+    for b in schwarz.boxes(p, (2, 2, 1, 2), 1):
+        idx, owned = schwarz.box_unknowns(p, b)
+        owner[idx[owned]] += 1
+        assert len(np.unique(idx)) == len(idx)
+    assert np.all(owner == 1)
+
+
+def test_ilu0_defining_property_on_pattern():
+    """(L U)_ij = a_ij for every (i, j) in the pattern (the definition of ILU(0))."""
+    p, F = _small()
+    b = schwarz.boxes(p, (2, 1, 1, 2), 1)[1]
+    idx, _ = schwarz.box_unknowns(p, b)
+    Aloc = F[idx][:, idx].toarray()
+    pat = schwarz.local_pattern(p, idx)
+    ilu = schwarz.ILU0(sp.csr_matrix(Aloc), pat)
+    n = len(idx)
+    Lm = np.eye(n)
+    Um = np.zeros((n, n))
+    for i in range(n):
+        for k, v in ilu.L[i].items():
+            Lm[i, k] = v
+        Um[i, i] = ilu.diag[i]
+        for j, v in ilu.U[i].items():
+            Um[i, j] = v
+    LU = Lm @ Um
+    mask = np.zeros((n, n), dtype=bool)
+    for i, cols in enumerate(pat):
+        mask[i, cols] = True
+    assert np.abs((LU - Aloc)[mask]).max() < 1e-13 * np.abs(Aloc).max()
+    # the factors live on the pattern only
+    assert not np.any(Lm[~mask & ~np.eye(n, dtype=bool)]) and not np.any(Um[~mask])
+    # every stored entry of F is inside the structural pattern
+    assert not np.any(Aloc[~mask])
+    # and it is not exact (the KKT pattern has fill)
+    assert np.abs(LU - Aloc).max() > 1e-8 * np.abs(Aloc).max()
+
+
+def test_ilu0_without_fill_is_exact_lu():
+    rng = np.random.default_rng(4)
+    n = 40
+    A = sp.diags([rng.normal(size=n - 1), 4 + rng.random(n), rng.normal(size=n - 1)], [-1, 0, 1]).tocsr()
+    pat = [np.array([j for j in (i - 1, i, i + 1) if 0 <= j < n]) for i in range(n)]
+    ilu = schwarz.ILU0(A, pat)
+    r = rng.normal(size=n)
+    assert np.allclose(ilu.solve(r), np.linalg.solve(A.toarray(), r), rtol=1e-13, atol=1e-13)
+
+
+def test_one_box_exact_lu_is_the_inverse_and_gmres_takes_one_step():
+    p, F = _small(cells=(2, 2, 2), M=2)
+    ras = schwarz.RAS(p, F, (1, 1, 1, 1), 0, "lu")
+    r = W.random_vector(p.n, 3)
+    assert np.allclose(F @ ras.apply(r), r, rtol=1e-11, atol=1e-11)
+    res = krylov.gmres(lambda u: F @ u, r, ras.apply, restart=10, rtol=1e-10)
+    assert res.iterations == 1 and res.converged
+
+
+def test_ras_variants_agree_without_overlap():
+    """With zero overlap R^delta = R^0, so both operand orders give block Jacobi."""
+    p, F = _small()
+    r = W.random_vector(p.n, 8)
+    a = schwarz.RAS(p, F, (2, 2, 1, 2), 0, "lu").apply(r)
+    b = schwarz.RAS(p, F, (2, 2, 1, 2), 0, "lu", variant="harmonic").apply(r)
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-13)
+
+
+def test_ras_with_overlap_is_a_better_preconditioner():
+    p, F = _small(cells=(4, 3, 3), M=5)
+    b = W.random_vector(p.n, 2)
+    its = []
+    for ov in (0, 1, 2):
+        ras = schwarz.RAS(p, F, (2, 2, 2, 2), ov, "lu")
+        its.append(krylov.gmres(lambda u: F @ u, b, ras.apply, restart=60, rtol=1e-8).iterations)
+    assert its[0] > its[1] >= its[2], its
+
+
+def test_interpolation_reproduces_multilinear_functions():
+    wf = W.random_small(1, cells=(4, 2, 6), M=4)
+    pf = kkt.Problem.from_workload(wf)
+    pc = schwarz.coarse_problem(pf, (2, 1, 3), 2)
+    P = schwarz.interpolation(pf, pc)
+
+    def field(p):
+        nx, ny, nz = p.nodes
+        h = [l / c for l, c in zip(p.lengths, p.cells)]
+        t, z, y, x = np.meshgrid(np.arange(p.L) * p.tau, np.arange(nz) * h[2], np.arange(ny) * h[1],
+                                 np.arange(nx) * h[0], indexing="ij")
+        base = (1 + 2 * x) * (3 - y) * (0.5 + z) * (2 + 5 * t)
+        return np.stack([base, -base, 2 * base], axis=-1).ravel()
+
+    assert np.allclose(P @ field(pc), field(pf), rtol=1e-13, atol=1e-13)
+    # injection after interpolation is the identity on the coarse points
+    Rinj = schwarz.injection(pf, pc)
+    assert np.allclose((Rinj @ P).toarray(), np.eye(pc.n))
+    # the transpose restriction preserves the weighted sum of each component
+    u = W.random_vector(pf.n, 4)
+    w = W.random_vector(pc.n, 5)
+    assert abs((P @ w) @ u - w @ (P.T @ u)) < 1e-12 * np.abs(u).sum()
+
+
+def test_coarse_problem_averages_and_resnaps():
+    wf = W.random_small(2, cells=(4, 4, 2), M=4, nsens=5)
+    pf = kkt.Problem.from_workload(wf)
+    pc = schwarz.coarse_problem(pf, (2, 2, 1), 2)
+    a = pf.a_cell.reshape(2, 4, 4)
+    assert np.isclose(pc.a_cell[0], a[0:2, 0:2, 0:2].mean())
+    assert np.isclose(pc.a_cell.mean(), pf.a_cell.mean())
+    assert np.allclose(pc.v_cell.mean(0), pf.v_cell.mean(0))
+    assert pc.s.sum() == pf.s.sum()
+
+
+def test_two_level_with_identical_coarse_mesh_and_exact_coarse_solve_is_exact():
+    p, F = _small(cells=(2, 2, 2), M=2, faces=W.FACE_X0)
+    tl = schwarz.TwoLevel(p, F, (2, 1, 1, 1), 1, p.cells, p.M, c_overlap=0, c_rtol=1e-14,
+                          c_maxit=200, local="ilu0")
+    tl.coarse = schwarz.RAS(tl.pc, tl.Fc, (1, 1, 1, 1), 0, "lu")
+    x = W.random_vector(p.n, 6)
+    z = tl.apply(x)
+    assert np.allclose(F @ z, x, rtol=1e-10, atol=1e-10 * np.abs(x).max())
+
+
+# ---------------------------------------------------------------------------
+# Krylov
+# ---------------------------------------------------------------------------
+
+def test_gmres_matches_dense_solve_with_restarts():
+    rng = np.random.default_rng(0)
+    n = 60
+    A = np.eye(n) * 3 + rng.normal(size=(n, n)) / np.sqrt(n)
+    b = rng.normal(size=n)
+    res = krylov.gmres(lambda u: A @ u, b, restart=10, rtol=1e-12, maxit=500)
+    assert res.converged
+    assert np.allclose(res.x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-10)
+
+
+def test_gmres_terminates_in_n_steps_without_restart():
+    rng = np.random.default_rng(1)
+    n = 12
+    A = rng.normal(size=(n, n)) + 0.1 * np.eye(n)
+    b = rng.normal(size=n)
+    res = krylov.gmres(lambda u: A @ u, b, restart=n, rtol=1e-10, maxit=n)
+    assert res.iterations <= n and res.relres < 1e-8
+
+
+def test_flexible_and_standard_gmres_agree_for_a_fixed_preconditioner():
+    rng = np.random.default_rng(2)
+    n = 50
+    A = np.eye(n) * 2 + rng.normal(size=(n, n)) / np.sqrt(n)
+    Minv = np.linalg.inv(np.diag(np.diag(A)) + np.triu(A, 1) * 0.5)
+    b = rng.normal(size=n)
+    r1 = krylov.gmres(lambda u: A @ u, b, lambda v: Minv @ v, restart=8, rtol=1e-10, maxit=300)
+    r2 = krylov.gmres(lambda u: A @ u, b, lambda v: Minv @ v, restart=8, rtol=1e-10, maxit=300, flexible=True)
+    assert r1.iterations == r2.iterations
+    assert np.allclose(r1.x, r2.x, rtol=1e-8, atol=1e-9)
+    # an exact preconditioner gives one step
+    r3 = krylov.gmres(lambda u: A @ u, b, lambda v: np.linalg.solve(A, v), restart=8, rtol=1e-10)
+    assert r3.iterations == 1
