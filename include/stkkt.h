@@ -1,0 +1,199 @@
+/*
+ * stkkt.h -- C ABI of the GB300 space-time KKT library.
+ *
+ * The library solves the all-at-once optimality (KKT) system of the 3D
+ * unsteady convection-diffusion inverse source problem of Deng, Cai and Zou,
+ * "Two-level space-time domain decomposition methods for unsteady inverse
+ * problems" (arXiv 1508.06103):
+ *
+ *   state   C_t = div(a grad C) - div(v C) + f     (Eq. 1)
+ *   misfit  J(f) = 1/2 int sum_i (C(x_i,t) - Ceps_i(t))^2 + N_beta(f)   (Eq. 2-3)
+ *
+ * discretised with trilinear (Q1) finite elements in space on a uniform box,
+ * a theta scheme in time (theta = 1/2 is the paper's Crank-Nicolson, Eq. 8)
+ * for the state C and adjoint G, and space-time linear elements for the
+ * source f (Eq. 9).  The discrete system F_h U = b (Sec. 3.2, Appendix) is
+ * solved by right-preconditioned (flexible) GMRES with the one-level
+ * space-time restricted additive Schwarz preconditioner (Sec. 3.2) or the
+ * two-level multiplicative hybrid with a coarse space-time GMRES solve.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Vectors use the paper's point-block order (Sec. 3.2):
+ *     U[((n * N + j) * 3 + c)],  c = 0 (C), 1 (G), 2 (f),
+ *     node j = ix + nx * (iy + ny * iz), level n = 0..M,  N = nx*ny*nz.
+ * Vector arguments are DEVICE pointers (memory of the current CUDA device,
+ * e.g. from torch) unless a parameter says "host".  The caller owns them;
+ * the library owns its handles and every internal buffer.  Calls are
+ * stream-ordered on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ * default stream) and do not synchronise, except where stated.
+ * Every call returns a kkt_status; on an error the output buffers are
+ * unspecified and kkt_last_error() describes the failure.  A *_destroy(NULL)
+ * is a no-op.  Handles are not thread-safe: one host thread per handle.
+ */
+#ifndef STKKT_H
+#define STKKT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int kkt_status;
+#define KKT_OK                 0
+#define KKT_NOT_CONVERGED      1   /* iteration limit reached            */
+#define KKT_BREAKDOWN          2   /* Krylov breakdown before tolerance  */
+#define KKT_ERR_ARG           -1   /* invalid argument                   */
+#define KKT_ERR_NOMEM         -2   /* device or host allocation failed   */
+#define KKT_ERR_CUDA          -3   /* CUDA runtime error                 */
+#define KKT_ERR_NONFINITE     -4   /* NaN/Inf met in the solver          */
+#define KKT_ERR_ZERO_PIVOT    -5   /* a subdomain factor hit a zero pivot */
+
+/* Face bits of the Dirichlet part Gamma_1 of the boundary (Eq. 1). */
+#define KKT_FACE_X0 1u
+#define KKT_FACE_X1 2u
+#define KKT_FACE_Y0 4u
+#define KKT_FACE_Y1 8u
+#define KKT_FACE_Z0 16u
+#define KKT_FACE_Z1 32u
+
+/* Uniform grid of cx*cy*cz hexahedral cells on [0,lx]x[0,ly]x[0,lz]. */
+typedef struct {
+  int cx, cy, cz;
+  double lx, ly, lz;
+  unsigned dirichlet_faces;   /* bit mask of KKT_FACE_*; the rest is Neumann */
+} kkt_grid;
+
+typedef struct kkt_problem kkt_problem;     /* opaque */
+typedef struct ras_precond ras_precond;     /* opaque */
+typedef struct coarse_level coarse_level;   /* opaque */
+
+/* Text of the last error on the calling thread (static storage). */
+const char* kkt_last_error(void);
+
+/* Library version string. */
+const char* kkt_version(void);
+
+/*
+ * kkt_create -- build the discrete KKT operator F_h (Sec. 3.1, Appendix).
+ *   g           grid and Dirichlet faces (host).
+ *   nt, dt      M = nt time steps of size tau = dt (levels 0..M).
+ *   a_cell      host, cx*cy*cz values of the diffusivity a at cell centroids
+ *               (cell id ex + cx*(ey + cy*ez)); a is constant per cell.
+ *   v_cell      host, 3*cx*cy*cz values (vx, vy, vz per cell) of the velocity.
+ *   sensor_node host, nsens node ids of the sensors (already snapped to nodes;
+ *               repeats count twice; sensors on Dirichlet nodes are ignored,
+ *               their rows being identity rows).  May be NULL if nsens == 0.
+ *   beta1, beta2 regularisation weights of N_beta (Eq. 3).
+ *   theta       time weight: 0.5 = Crank-Nicolson (Eq. 8), 1 = implicit Euler;
+ *               must lie in [0.5, 1].
+ *   out         receives the handle.
+ * Runs synchronously (uploads the stencil coefficients); errors: ARG, NOMEM, CUDA.
+ */
+kkt_status kkt_create(const kkt_grid* g, int nt, double dt, const double* a_cell,
+                      const double* v_cell, const int* sensor_node, int nsens,
+                      double beta1, double beta2, double theta, kkt_problem** out);
+
+/* Sizes of a problem: nodes per axis, N, levels M+1 and unknowns 3*N*(M+1). */
+kkt_status kkt_sizes(const kkt_problem* p, int* nx, int* ny, int* nz, int* levels,
+                     long long* unknowns);
+
+/*
+ * kkt_rhs -- right-hand side b of F_h U = b (Appendix):
+ *   C slot at level 0 = c0 (zero if c0 == NULL; zero on Dirichlet nodes),
+ *   G slot at level n < M = tau * sum_{sensors k at node j}
+ *                            ((1-theta) c_obs[n][k] + theta c_obs[n+1][k]),
+ *   every other slot 0 (homogeneous Dirichlet data p and Neumann data q).
+ *   c_obs  device, (M+1) x nsens observations Ceps, row = time level.
+ *   c0     device, N initial values, or NULL.
+ *   b      device, 3*N*(M+1) output.
+ */
+kkt_status kkt_rhs(kkt_problem* p, const double* c_obs, const double* c0, double* b, void* stream);
+
+/*
+ * kkt_apply -- y = F_h x, the KKT matvec (Appendix block rows, Eq. 8-9),
+ *   one fused 4D stencil pass over C, G and f.
+ *   precision 64: x, y are double*;  32: x, y are float* (FP32 arithmetic).
+ *   x and y must not overlap.
+ */
+kkt_status kkt_apply(kkt_problem* p, const void* x, void* y, int precision, void* stream);
+
+/*
+ * kkt_residual -- r = b - F_h x in FP64 (the true residual of Sec. 4's stop test).
+ */
+kkt_status kkt_residual(kkt_problem* p, const double* b, const double* x, double* r, void* stream);
+
+/*
+ * ras_setup -- one-level space-time restricted additive Schwarz preconditioner
+ *   (Sec. 3.2): nsub[0..3] = subdomains along x, y, z and time (part k of n
+ *   nodes or levels holds floor(n/p) + (k < n mod p)); each box is extended
+ *   by `overlap` nodes/levels per side and trimmed to the domain.  The
+ *   subdomain matrix is the principal submatrix of F_h on the extended box
+ *   (homogeneous Dirichlet conditions on all cut space and time faces,
+ *   Eq. 10-12) and is factored by ILU(0) on its structural pattern.
+ *   local        0 = ILU(0) (the only local solver of this version).
+ *   factor_prec  64 = factor and solve in FP64, 32 = FP32.
+ *   All boxes factor in one launch, synchronously; errors: ARG, NOMEM, CUDA,
+ *   ZERO_PIVOT.
+ */
+kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
+                     ras_precond** out);
+
+/*
+ * ras_apply -- z = sum_ij (R^0_ij)^T M_ij^{-1} R^delta_ij r (restricted prolongation,
+ *   Cai-Sarkis form cited in Sec. 3.2); all boxes in one launch.  r, z FP64, must
+ *   not overlap.
+ */
+kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream);
+
+/*
+ * coarse_setup -- the coarse space-time level of the two-level method (Sec. 3.2):
+ *   a nested coarse mesh of ccx x ccy x ccz cells and cnt steps (each must
+ *   divide the fine one), rediscretised with cell-mean a and v and with each
+ *   fine sensor node snapped to the nearest coarse node; a one-level RAS on
+ *   it with nsub_c subdomains and overlap c_overlap; interpolation I^h_c
+ *   multilinear in (x, y, z, t) and restriction I^c_h = (I^h_c)^T; the coarse
+ *   solve F_c^{-1} is GMRES right-preconditioned by that RAS, stopped at
+ *   relative residual c_rtol or after c_maxit iterations.  Synchronous.
+ */
+kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz, int cnt, const int nsub_c[4],
+                        int c_overlap, double c_rtol, int c_maxit, int factor_prec,
+                        coarse_level** out);
+
+/*
+ * two_level_apply -- z = y + M_one^{-1}(x - F_h y), y = I^h_c F_c^{-1} I^c_h x
+ *   (the multiplicative hybrid of Sec. 3.2).  Synchronises the stream once
+ *   per coarse GMRES iteration.
+ */
+kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const double* x, double* z, void* stream);
+
+/*
+ * gmres_solve -- right-preconditioned restarted GMRES(restart) (flexible when
+ *   `flexible` != 0, required with a coarse level) for F_h x = b (Sec. 3.2, 4).
+ *   Orthogonalisation is classical Gram-Schmidt applied twice; Arnoldi vectors,
+ *   Givens rotations and the true residual are FP64.  The method stops when
+ *   the true residual ||b - F_h x||_2 <= rtol ||b||_2 (checked when the
+ *   Arnoldi estimate passes) or after maxit iterations.
+ *   m      one-level preconditioner or NULL (unpreconditioned).
+ *   c      coarse level or NULL (one-level).
+ *   x      device FP64; holds the initial guess on entry (zero in the paper).
+ *   iters, true_relres  host outputs (may be NULL).
+ *   Synchronises the stream; returns OK, NOT_CONVERGED, BREAKDOWN or an error.
+ */
+kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* c, const double* b, double* x,
+                       int restart, double rtol, int maxit, int flexible, int* iters,
+                       double* true_relres, void* stream);
+
+/*
+ * recover_source -- f of the point-block vector U as an (M+1) x N array
+ *   (Sec. 3.2 ordering; the recovered source of the inverse problem).
+ */
+kkt_status recover_source(kkt_problem* p, const double* U, double* f, void* stream);
+
+void kkt_destroy(kkt_problem* p);
+void ras_destroy(ras_precond* m);
+void coarse_destroy(coarse_level* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STKKT_H */

@@ -1,0 +1,178 @@
+"""Python binding of the C ABI with torch tensors for device memory and streams.
+
+Each wrapper only marshals arguments (pointers, sizes, the current CUDA
+stream) and calls the library; the arithmetic runs in the CUDA kernels.
+Vectors are 1-D torch tensors on the current CUDA device in the paper's
+point-block order U[((n*N + j)*3 + c)] (c = C, G, f).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _stream(stream: Optional[torch.cuda.Stream] = None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=torch.float64) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(None)
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """Handle of one discrete KKT system F_h (kkt_create)."""
+
+    def __init__(self, cells: Sequence[int], lengths: Sequence[float], nt: int, dt: float,
+                 a_cell: np.ndarray, v_cell: np.ndarray, sensor_node: np.ndarray, beta1: float, beta2: float,
+                 theta: float = 0.5, dirichlet_faces: int = 1):
+        self._lib = _lib.load()
+        g = _lib.KktGrid(int(cells[0]), int(cells[1]), int(cells[2]), float(lengths[0]), float(lengths[1]),
+                         float(lengths[2]), int(dirichlet_faces))
+        a = np.ascontiguousarray(a_cell, dtype=np.float64)
+        v = np.ascontiguousarray(v_cell, dtype=np.float64).reshape(-1)
+        s = np.ascontiguousarray(sensor_node, dtype=np.int32)
+        h = C.c_void_p()
+        check(self._lib.kkt_create(C.byref(g), int(nt), float(dt), a.ctypes.data_as(C.c_void_p),
+                                   v.ctypes.data_as(C.c_void_p),
+                                   s.ctypes.data_as(C.c_void_p) if s.size else None, int(s.size),
+                                   float(beta1), float(beta2), float(theta), C.byref(h)), "kkt_create")
+        self.h = h
+        nx, ny, nz, lv = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        n = C.c_longlong()
+        check(self._lib.kkt_sizes(h, C.byref(nx), C.byref(ny), C.byref(nz), C.byref(lv), C.byref(n)), "kkt_sizes")
+        self.nodes = (nx.value, ny.value, nz.value)
+        self.N = nx.value * ny.value * nz.value
+        self.levels = lv.value
+        self.n = n.value
+        self.nsens = int(s.size)
+
+    @classmethod
+    def from_workload(cls, w, cells=None, M=None) -> "Problem":
+        return cls(w.cells, w.lengths, w.M, w.tau, w.a_cell, w.v_cell, w.sensor_nodes(), w.beta1, w.beta2,
+                   w.theta, w.dirichlet_faces)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self._lib.kkt_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- vectors -------------------------------------------------------------
+    def zeros(self, dtype=torch.float64) -> torch.Tensor:
+        return torch.zeros(self.n, dtype=dtype, device="cuda")
+
+    def rhs(self, c_obs: torch.Tensor, c0: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+        b = out if out is not None else self.zeros()
+        check(self._lib.kkt_rhs(self.h, _ptr(c_obs.contiguous()) if self.nsens else None, _ptr(c0), _ptr(b),
+                                _stream(stream)), "kkt_rhs")
+        return b
+
+    def apply(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        prec = 64 if x.dtype == torch.float64 else 32
+        y = out if out is not None else torch.empty_like(x)
+        check(self._lib.kkt_apply(self.h, _ptr(x, x.dtype), _ptr(y, x.dtype), prec, _stream(stream)), "kkt_apply")
+        return y
+
+    def residual(self, b: torch.Tensor, x: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 stream=None) -> torch.Tensor:
+        r = out if out is not None else torch.empty_like(b)
+        check(self._lib.kkt_residual(self.h, _ptr(b), _ptr(x), _ptr(r), _stream(stream)), "kkt_residual")
+        return r
+
+    def recover_source(self, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        f = out if out is not None else torch.empty(self.levels * self.N, dtype=torch.float64, device="cuda")
+        check(self._lib.recover_source(self.h, _ptr(U), _ptr(f), _stream(stream)), "recover_source")
+        return f.view(self.levels, self.N)
+
+
+class RAS:
+    """One-level space-time RAS with ILU(0) subdomain solves (ras_setup)."""
+
+    def __init__(self, prob: Problem, nsub: Sequence[int], overlap: int, factor_prec: int = 64):
+        self._lib = _lib.load()
+        self.prob = prob
+        ns = (C.c_int * 4)(*[int(v) for v in nsub])
+        h = C.c_void_p()
+        check(self._lib.ras_setup(prob.h, ns, int(overlap), 0, int(factor_prec), C.byref(h)), "ras_setup")
+        self.h = h
+
+    def apply(self, r: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        z = out if out is not None else torch.empty_like(r)
+        check(self._lib.ras_apply(self.h, _ptr(r), _ptr(z), _stream(stream)), "ras_apply")
+        return z
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self._lib.ras_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Coarse:
+    """Coarse space-time level of the two-level method (coarse_setup)."""
+
+    def __init__(self, prob: Problem, ccells: Sequence[int], cnt: int, nsub_c: Sequence[int], c_overlap: int = 1,
+                 c_rtol: float = 0.1, c_maxit: int = 4, factor_prec: int = 64):
+        self._lib = _lib.load()
+        self.prob = prob
+        ns = (C.c_int * 4)(*[int(v) for v in nsub_c])
+        h = C.c_void_p()
+        check(self._lib.coarse_setup(prob.h, int(ccells[0]), int(ccells[1]), int(ccells[2]), int(cnt), ns,
+                                     int(c_overlap), float(c_rtol), int(c_maxit), int(factor_prec), C.byref(h)),
+              "coarse_setup")
+        self.h = h
+
+    def apply(self, fine: RAS, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        z = out if out is not None else torch.empty_like(x)
+        check(self._lib.two_level_apply(self.h, fine.h, _ptr(x), _ptr(z), _stream(stream)), "two_level_apply")
+        return z
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self._lib.coarse_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gmres_solve(prob: Problem, b: torch.Tensor, x: Optional[torch.Tensor] = None, ras: Optional[RAS] = None,
+                coarse: Optional[Coarse] = None, restart: int = 30, rtol: float = 1e-8, maxit: int = 1000,
+                flexible: Optional[bool] = None, stream=None):
+    """Solve F_h x = b; returns (x, status, iterations, true relative residual)."""
+    lib = _lib.load()
+    if x is None:
+        x = torch.zeros_like(b)
+    flex = (coarse is not None) if flexible is None else bool(flexible)
+    it = C.c_int()
+    rel = C.c_double()
+    st = lib.gmres_solve(prob.h, ras.h if ras else None, coarse.h if coarse else None, _ptr(b), _ptr(x),
+                         int(restart), float(rtol), int(maxit), int(flex), C.byref(it), C.byref(rel), _stream(stream))
+    check(st, "gmres_solve")
+    return x, st, it.value, rel.value

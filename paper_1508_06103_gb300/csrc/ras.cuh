@@ -1,0 +1,42 @@
+// Internal declarations of the Schwarz preconditioner.
+#pragma once
+
+#include "internal.cuh"
+
+// slots per point: C row 2*27*2 = 108, G row 2*(27+1) = 56, f row 3*27*2 = 162
+constexpr int kSlots = 326;
+
+// One subdomain box (extended set, owned set, storage offsets).
+struct BoxDesc {
+  int x0, y0, z0, t0;          // origin of the extended box (global node / level)
+  int lx, ly, lz, lt;          // extended box extents
+  int ox0, ox1, oy0, oy1, oz0, oz1, ot0, ot1;   // owned ranges (global, half open)
+  int nlev;                    // wavefronts x + 2y + 4z + 8t
+  long long P;                 // points of the extended box
+  long long foff;              // offset of the box's factor values (elements)
+  long long voff;              // offset of the box's padded local vector (elements)
+  long long poff;              // offset into perm / iperm
+  long long loff;              // offset into the wavefront pointers
+};
+
+struct ras_precond {
+  kkt_problem* prob = nullptr;
+  int prec = 64;               // factor / solve precision (64 or 32)
+  int nbox = 0;
+  long long fcount = 0;        // factor values
+  std::vector<BoxDesc> boxes_h;
+  BoxDesc* boxes = nullptr;
+  int* perm = nullptr;         // wavefront order -> lexicographic local index
+  int* iperm = nullptr;        // lexicographic -> wavefront order
+  int* lptr = nullptr;         // wavefront pointers per box (nlev + 1 each)
+  int* uptr = nullptr;         // factorisation update lists
+  short2* upd = nullptr;
+  void* F = nullptr;           // factor values
+  void* V = nullptr;           // padded local vectors
+  int* status = nullptr;
+};
+
+kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
+                      ras_precond** out);
+kkt_status ras_factor(ras_precond* m);
+kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s);

@@ -1,0 +1,286 @@
+// Two-level space-time Schwarz preconditioner and the outer solver (Sec. 3.2, 4).
+//
+// Coarse level.  The coarse space-time mesh is nested in the fine one (every
+// coarse node and level is a fine node and level).  The coarse operator F_c is
+// rediscretised on it: a and v of a coarse cell are the means over its fine
+// cells and each fine sensor node goes to the nearest coarse node (ties toward
+// the lower index).  Interpolation I^h_c is multilinear in (x, y, z, t) and
+// acts on C, G and f alike; restriction is its transpose I^c_h = (I^h_c)^T.
+//
+// Two-level multiplicative hybrid:
+//   y = I^h_c F_c^{-1} I^c_h x,   z = y + M_one^{-1} (x - F_h y),
+// where F_c^{-1} is GMRES right-preconditioned by the coarse one-level RAS,
+// stopped at relative residual c_rtol or after c_maxit iterations; since it
+// changes with x the outer solver is flexible GMRES.
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+#include "ras.cuh"
+
+struct coarse_level {
+  kkt_problem* fine = nullptr;
+  kkt_problem* cp = nullptr;         // coarse problem (owned)
+  ras_precond* cras = nullptr;       // coarse one-level RAS (owned)
+  int rx = 1, ry = 1, rz = 1, rt = 1;
+  double c_rtol = 0.1;
+  int c_maxit = 4;
+  double *rc = nullptr, *yc = nullptr, *y = nullptr, *t = nullptr;
+  GmresWork ws;
+  int last_coarse_iters = 0;
+};
+
+namespace {
+
+struct Grid4 {
+  int nx, ny, nz, L, N;
+};
+
+// fine y = I^h_c yc (multilinear in x, y, z, t); one thread per fine point
+__global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ yc,
+                              double* __restrict__ y) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)f.N * f.L) return;
+  const int n = (int)(idx / f.N);
+  const int j = (int)(idx - (long long)n * f.N);
+  const int ix = j % f.nx, iy = (j / f.nx) % f.ny, iz = j / (f.nx * f.ny);
+  int I[4][2];
+  double W[4][2];
+  int cnt[4];
+  const int pos[4] = {ix, iy, iz, n}, rr[4] = {rx, ry, rz, rt}, cn[4] = {c.nx, c.ny, c.nz, c.L};
+  for (int a = 0; a < 4; ++a) {
+    const int q = pos[a] / rr[a], rem = pos[a] - q * rr[a];
+    I[a][0] = q;
+    if (rem == 0) {
+      W[a][0] = 1.0;
+      cnt[a] = 1;
+    } else {
+      W[a][0] = 1.0 - (double)rem / rr[a];
+      I[a][1] = min(q + 1, cn[a] - 1);
+      W[a][1] = (double)rem / rr[a];
+      cnt[a] = 2;
+    }
+  }
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int at = 0; at < cnt[3]; ++at)
+    for (int az = 0; az < cnt[2]; ++az)
+      for (int ay = 0; ay < cnt[1]; ++ay)
+        for (int ax = 0; ax < cnt[0]; ++ax) {
+          const double w = W[0][ax] * W[1][ay] * W[2][az] * W[3][at];
+          const long long jc = I[0][ax] + (long long)c.nx * (I[1][ay] + (long long)c.ny * I[2][az]);
+          const double* src = yc + 3 * ((long long)I[3][at] * c.N + jc);
+          acc[0] += w * src[0];
+          acc[1] += w * src[1];
+          acc[2] += w * src[2];
+        }
+  y[3 * idx] = acc[0];
+  y[3 * idx + 1] = acc[1];
+  y[3 * idx + 2] = acc[2];
+}
+
+// coarse rc = (I^h_c)^T x; one thread per coarse point gathers its fine support
+__global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ x,
+                                double* __restrict__ rc) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)c.N * c.L) return;
+  const int n = (int)(idx / c.N);
+  const int j = (int)(idx - (long long)n * c.N);
+  const int I = j % c.nx, J = (j / c.nx) % c.ny, K = j / (c.nx * c.ny);
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int at = -rt + 1; at <= rt - 1; ++at) {
+    const int ft = n * rt + at;
+    if (ft < 0 || ft >= f.L) continue;
+    const double wt = 1.0 - (double)abs(at) / rt;
+    for (int az = -rz + 1; az <= rz - 1; ++az) {
+      const int fz = K * rz + az;
+      if (fz < 0 || fz >= f.nz) continue;
+      const double wz = wt * (1.0 - (double)abs(az) / rz);
+      for (int ay = -ry + 1; ay <= ry - 1; ++ay) {
+        const int fy = J * ry + ay;
+        if (fy < 0 || fy >= f.ny) continue;
+        const double wy = wz * (1.0 - (double)abs(ay) / ry);
+        for (int ax = -rx + 1; ax <= rx - 1; ++ax) {
+          const int fx = I * rx + ax;
+          if (fx < 0 || fx >= f.nx) continue;
+          const double w = wy * (1.0 - (double)abs(ax) / rx);
+          const double* src = x + 3 * ((long long)ft * f.N + fx + (long long)f.nx * (fy + (long long)f.ny * fz));
+          acc[0] += w * src[0];
+          acc[1] += w * src[1];
+          acc[2] += w * src[2];
+        }
+      }
+    }
+  }
+  rc[3 * idx] = acc[0];
+  rc[3 * idx + 1] = acc[1];
+  rc[3 * idx + 2] = acc[2];
+}
+
+Grid4 grid_of(const kkt_problem* p) { return Grid4{p->nx, p->ny, p->nz, p->L, p->N}; }
+
+struct KktOp : Operator {
+  kkt_problem* p;
+  explicit KktOp(kkt_problem* p_) : p(p_) {}
+  kkt_status apply(const double* x, double* y, cudaStream_t s) override { return launch_matvec64(p->dev(), x, y, s); }
+};
+
+struct RasOp : Operator {
+  ras_precond* m;
+  explicit RasOp(ras_precond* m_) : m(m_) {}
+  kkt_status apply(const double* x, double* y, cudaStream_t s) override { return ras_launch(m, x, y, s); }
+};
+
+kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double* z, cudaStream_t s) {
+  kkt_problem* pf = c->fine;
+  kkt_problem* pc = c->cp;
+  const Grid4 gf = grid_of(pf), gc = grid_of(pc);
+  restrict_kernel<<<(unsigned)((pc->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
+  KKT_TRY_CUDA(cudaGetLastError());
+  KktOp Ac(pc);
+  RasOp Mc(c->cras);
+  GmresResult r;
+  KKT_TRY(gmres_run(Ac, &Mc, c->rc, c->yc, c->ws, c->c_maxit, c->c_rtol, c->c_maxit, false, true, &r, s));
+  if (r.status < 0) return r.status;
+  c->last_coarse_iters = r.iters;
+  interp_kernel<<<(unsigned)((pf->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
+  KKT_TRY_CUDA(cudaGetLastError());
+  KKT_TRY(launch_residual(pf->dev(), x, c->y, c->t, s));   // t = x - F_h y
+  KKT_TRY(ras_launch(fine, c->t, z, s));
+  KKT_TRY(vec_axpby(z, 1.0, c->y, 1.0, pf->n, s));          // z = M^{-1} t + y
+  return KKT_OK;
+}
+
+struct TwoLevelOp : Operator {
+  coarse_level* c;
+  ras_precond* fine;
+  TwoLevelOp(coarse_level* c_, ras_precond* f_) : c(c_), fine(f_) {}
+  kkt_status apply(const double* x, double* y, cudaStream_t s) override { return two_level(c, fine, x, y, s); }
+};
+
+}  // namespace
+
+extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz, int cnt, const int nsub_c[4],
+                                   int c_overlap, double c_rtol, int c_maxit, int factor_prec, coarse_level** out) {
+  if (!fine || !nsub_c || !out) {
+    set_error("coarse_setup: null argument");
+    return KKT_ERR_ARG;
+  }
+  *out = nullptr;
+  const kkt_grid& g = fine->grid;
+  if (ccx < 1 || ccy < 1 || ccz < 1 || cnt < 1 || g.cx % ccx || g.cy % ccy || g.cz % ccz || fine->M % cnt ||
+      c_maxit < 1 || !(c_rtol > 0)) {
+    set_error("coarse_setup: the coarse mesh must be nested (divisors of the fine cells and steps)");
+    return KKT_ERR_ARG;
+  }
+  coarse_level* c = new (std::nothrow) coarse_level();
+  if (!c) return KKT_ERR_NOMEM;
+  c->fine = fine;
+  c->rx = g.cx / ccx;
+  c->ry = g.cy / ccy;
+  c->rz = g.cz / ccz;
+  c->rt = fine->M / cnt;
+  c->c_rtol = c_rtol;
+  c->c_maxit = c_maxit;
+  // coarse coefficients: cell means of the fine cells
+  const int ncc = ccx * ccy * ccz;
+  std::vector<double> ac(ncc, 0.0), vc(3 * (size_t)ncc, 0.0);
+  const double inv = 1.0 / ((double)c->rx * c->ry * c->rz);
+  for (int ez = 0; ez < g.cz; ++ez)
+    for (int ey = 0; ey < g.cy; ++ey)
+      for (int ex = 0; ex < g.cx; ++ex) {
+        const int e = ex + g.cx * (ey + g.cy * ez);
+        const int E = ex / c->rx + ccx * (ey / c->ry + ccy * (ez / c->rz));
+        ac[E] += inv * fine->a_cell[e];
+        for (int d = 0; d < 3; ++d) vc[3 * (size_t)E + d] += inv * fine->v_cell[3 * (size_t)e + d];
+      }
+  // sensors: nearest coarse node of each fine sensor node, ties toward the lower index
+  std::vector<int> sc(fine->sensor_node.size());
+  auto snap = [](int i, int r) { return (i + (r - 1) / 2) / r; };
+  for (size_t q = 0; q < sc.size(); ++q) {
+    const int j = fine->sensor_node[q];
+    const int ix = j % fine->nx, iy = (j / fine->nx) % fine->ny, iz = j / (fine->nx * fine->ny);
+    sc[q] = snap(ix, c->rx) + (ccx + 1) * (snap(iy, c->ry) + (ccy + 1) * snap(iz, c->rz));
+  }
+  kkt_grid cg = g;
+  cg.cx = ccx;
+  cg.cy = ccy;
+  cg.cz = ccz;
+  kkt_status st = create_problem(&cg, cnt, fine->tau * c->rt, ac.data(), vc.data(), sc.empty() ? nullptr : sc.data(),
+                                 (int)sc.size(), fine->beta1, fine->beta2, fine->theta, &c->cp);
+  if (st == KKT_OK) st = ras_create(c->cp, nsub_c, c_overlap, 0, factor_prec, &c->cras);
+  if (st == KKT_OK) st = c->ws.alloc(c->cp->n, c_maxit, false);
+  if (st == KKT_OK &&
+      (cudaMalloc(&c->rc, c->cp->n * sizeof(double)) != cudaSuccess ||
+       cudaMalloc(&c->yc, c->cp->n * sizeof(double)) != cudaSuccess ||
+       cudaMalloc(&c->y, fine->n * sizeof(double)) != cudaSuccess ||
+       cudaMalloc(&c->t, fine->n * sizeof(double)) != cudaSuccess)) {
+    cudaGetLastError();
+    set_error("coarse_setup: device allocation failed");
+    st = KKT_ERR_NOMEM;
+  }
+  if (st != KKT_OK) {
+    coarse_destroy(c);
+    return st;
+  }
+  *out = c;
+  return KKT_OK;
+}
+
+extern "C" kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const double* x, double* z, void* stream) {
+  if (!c || !fine || !x || !z || x == z) {
+    set_error("two_level_apply: bad argument");
+    return KKT_ERR_ARG;
+  }
+  if (fine->prob != c->fine) {
+    set_error("two_level_apply: the fine preconditioner belongs to another problem");
+    return KKT_ERR_ARG;
+  }
+  return two_level(c, fine, x, z, (cudaStream_t)stream);
+}
+
+extern "C" void coarse_destroy(coarse_level* c) {
+  if (!c) return;
+  ras_destroy(c->cras);
+  kkt_destroy(c->cp);
+  cudaFree(c->rc);
+  cudaFree(c->yc);
+  cudaFree(c->y);
+  cudaFree(c->t);
+  c->ws.release();
+  delete c;
+}
+
+extern "C" kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* c, const double* b, double* x,
+                                  int restart, double rtol, int maxit, int flexible, int* iters, double* true_relres,
+                                  void* stream) {
+  if (!p || !b || !x || b == x || restart < 1 || maxit < 0 || !(rtol > 0)) {
+    set_error("gmres_solve: bad argument");
+    return KKT_ERR_ARG;
+  }
+  if (c && (!m || !flexible)) {
+    set_error("gmres_solve: the two-level method needs a fine RAS and flexible GMRES");
+    return KKT_ERR_ARG;
+  }
+  if ((m && m->prob != p) || (c && c->fine != p)) {
+    set_error("gmres_solve: preconditioner built for another problem");
+    return KKT_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!p->ws) {
+    p->ws = new (std::nothrow) GmresWork();
+    if (!p->ws) return KKT_ERR_NOMEM;
+  }
+  GmresWork& ws = *p->ws;
+  KKT_TRY(ws.alloc(p->n, restart, flexible != 0));
+  KktOp A(p);
+  RasOp R(m);
+  TwoLevelOp T(c, m);
+  Operator* M = c ? (Operator*)&T : (m ? (Operator*)&R : nullptr);
+  GmresResult res;
+  KKT_TRY(gmres_run(A, M, b, x, ws, restart, rtol, maxit, true, false, &res, s));
+  if (iters) *iters = res.iters;
+  if (true_relres) *true_relres = res.relres;
+  return res.status;
+}

@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every symbol include/stkkt.h declares (no GPU needed)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "stkkt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1508_06103_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_documented_entry_points():
+    names = _declared()
+    for n in ("kkt_create", "kkt_apply", "kkt_rhs", "ras_setup", "ras_apply", "coarse_setup", "gmres_solve",
+              "recover_source", "kkt_destroy", "ras_destroy", "coarse_destroy", "two_level_apply", "kkt_residual"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_binding_signatures_cover_the_header(lib):
+    from paper_1508_06103_gb300 import _lib
+
+    assert set(_declared()) == set(_lib.SIGNATURES)
+
+
+def test_version_and_error_strings(lib):
+    assert b"sm_103a" in lib.kkt_version()
+    assert isinstance(lib.kkt_last_error(), bytes)
+
+
+def test_destroy_null_is_a_noop(lib):
+    lib.kkt_destroy(None)
+    lib.ras_destroy(None)
+    lib.coarse_destroy(None)
+
+
+def test_argument_errors_are_reported_without_a_gpu(lib):
+    from paper_1508_06103_gb300 import _lib
+
+    h = ctypes.c_void_p()
+    # null grid -> KKT_ERR_ARG, no device work attempted
+    assert lib.kkt_create(None, 4, 0.25, None, None, None, 0, 1e-3, 1e-1, 0.5, ctypes.byref(h)) == -1
+    g = _lib.KktGrid(2, 2, 2, 1.0, 1.0, 1.0, 1)
+    a = (ctypes.c_double * 8)(*([0.1] * 8))
+    v = (ctypes.c_double * 24)()
+    # theta outside [1/2, 1]
+    assert lib.kkt_create(ctypes.byref(g), 4, 0.25, a, v, None, 0, 1e-3, 1e-1, 0.2, ctypes.byref(h)) == -1
+    # sensor out of range
+    s = (ctypes.c_int * 1)(999)
+    assert lib.kkt_create(ctypes.byref(g), 4, 0.25, a, v, s, 1, 1e-3, 1e-1, 0.5, ctypes.byref(h)) == -1
+    assert b"sensor" in lib.kkt_last_error()
+    assert lib.kkt_apply(None, None, None, 64, None) == -1
+    assert lib.gmres_solve(None, None, None, None, None, 30, 1e-8, 10, 0, None, None, None) == -1

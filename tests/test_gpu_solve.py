@@ -1,0 +1,159 @@
+"""GPU parity of the Schwarz preconditioners and the (F)GMRES solves against the oracle.
+
+Tolerances:
+* one-level RAS, FP64 factors: the GPU and the oracle run the same ILU(0)
+  (same pattern, same IKJ update order) and the same triangular sweeps, so
+  they differ only by rounding order; relative to max|z| the difference is
+  bounded by (number of terms per row ~ 330) x u x (growth of the factors).
+  The check is max|dz| <= 1e-9 max|z|.
+* two-level apply, FP64: also runs the 4-step coarse GMRES (CGS2) on both
+  sides; same bound.
+* FP64 solve: the benchmark spec's bound, relative 2-norm error of U <= 1e-8
+  against the oracle's sparse direct solve, after solving to rtol 1e-13 (the
+  KKT matrix is ill-conditioned, so a 1e-8 residual alone does not give a
+  1e-8 error).
+* mixed solve (FP32 factors, FP64 Krylov): recovered source f within 1e-5
+  relative L2 of the oracle's direct solve, after solving to rtol 1e-10.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+from oracle import forward as ofwd
+from oracle import kkt as okkt
+from oracle import schwarz as osch
+from paper_1508_06103_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1508_06103_gb300 import api as _api
+    from paper_1508_06103_gb300 import build
+
+    build.build()
+    return _api
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+RAS_CASES = [
+    dict(w=dict(seed=1, cells=(5, 4, 3), M=6, theta=0.5, dirichlet_faces=W.FACE_X0), nsub=(2, 2, 1, 2), ov=1),
+    dict(w=dict(seed=2, cells=(7, 3, 5), M=5, theta=1.0, dirichlet_faces=W.ALL_FACES), nsub=(3, 2, 2, 3), ov=2),
+    dict(w=dict(seed=3, cells=(4, 4, 2), M=3, theta=0.5, dirichlet_faces=0), nsub=(1, 1, 1, 1), ov=0),
+]
+
+
+@pytest.mark.parametrize("case", RAS_CASES, ids=["2x2x1x2", "3x2x2x3-ov2", "single"])
+def test_ras_apply_fp64_matches_oracle(api, case):
+    w = W.random_small(nsens=6, **case["w"])
+    p = okkt.Problem.from_workload(w)
+    F = okkt.assemble(p)
+    ref = osch.RAS(p, F, case["nsub"], case["ov"], "ilu0")
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, case["nsub"], case["ov"], 64)
+    for seed in (1, 2):
+        r = W.random_vector(prob.n, seed)
+        z = ras.apply(_dev(r)).cpu().numpy()
+        zr = ref.apply(r)
+        assert np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
+
+
+def test_ras_apply_fp32_close_to_oracle(api):
+    case = RAS_CASES[0]
+    w = W.random_small(nsens=6, **case["w"])
+    p = okkt.Problem.from_workload(w)
+    ref = osch.RAS(p, okkt.assemble(p), case["nsub"], case["ov"], "ilu0")
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, case["nsub"], case["ov"], 32)
+    r = W.random_vector(prob.n, 3)
+    zr = ref.apply(r)
+    z = ras.apply(_dev(r)).cpu().numpy()
+    assert np.linalg.norm(z - zr) <= 1e-3 * np.linalg.norm(zr)
+
+
+def _two_level_case():
+    return W.mid(cells=(4, 4, 4), M=8, nsub=(2, 2, 2, 2), overlap=1, coarse_cells=(2, 2, 2), coarse_M=4)
+
+
+def test_two_level_apply_fp64_matches_oracle(api):
+    w = _two_level_case()
+    p = okkt.Problem.from_workload(w)
+    F = okkt.assemble(p)
+    ref = osch.TwoLevel(p, F, w.nsub, w.overlap, w.coarse_cells, w.coarse_M, 1, 0.1, 4, "ilu0")
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, w.nsub, w.overlap, 64)
+    coarse = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, 1, 0.1, 4, 64)
+    x = W.random_vector(prob.n, 5)
+    z = coarse.apply(ras, _dev(x)).cpu().numpy()
+    zr = ref.apply(x)
+    assert np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
+
+
+def _exact(w):
+    p = okkt.Problem.from_workload(w)
+    F = okkt.assemble(p)
+    C = ofwd.forward_march(p, w.true_source())
+    cobs = ofwd.observations(p, C, w.noise(), w.noise_eps)
+    b = okkt.rhs(p, cobs)
+    return p, F, cobs, b, spla.spsolve(F.tocsc(), b)
+
+
+def test_one_level_fp64_solve_matches_direct_solve(api):
+    w = W.mid(cells=(4, 4, 4), M=6, nsub=(2, 2, 1, 2), overlap=1, coarse_cells=None, coarse_M=None)
+    p, F, cobs, b, U = _exact(w)
+    prob = api.Problem.from_workload(w)
+    bd = prob.rhs(_dev(cobs))
+    assert np.allclose(bd.cpu().numpy(), b, rtol=1e-14, atol=1e-18)
+    ras = api.RAS(prob, w.nsub, w.overlap, 64)
+    x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, restart=30, rtol=1e-13, maxit=2000)
+    assert st == 0 and rel <= 1e-13
+    xe = x.cpu().numpy()
+    assert np.linalg.norm(xe - U) <= 1e-8 * np.linalg.norm(U)
+    assert np.linalg.norm(b - F @ xe) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_two_level_solve_matches_direct_solve(api, prec):
+    w = W.mid(cells=(6, 6, 6), M=6, nsub=(2, 2, 2, 2), overlap=1, coarse_cells=(3, 3, 3), coarse_M=3)
+    p, F, cobs, b, U = _exact(w)
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, w.nsub, w.overlap, prec)
+    coarse = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, 1, 0.1, 4, prec)
+    bd = prob.rhs(_dev(cobs))
+    rtol = 1e-13 if prec == 64 else 1e-10
+    x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, coarse=coarse, restart=30, rtol=rtol, maxit=3000)
+    assert st == 0 and rel <= rtol
+    xe = x.cpu().numpy()
+    if prec == 64:
+        assert np.linalg.norm(xe - U) <= 1e-8 * np.linalg.norm(U)
+    f = prob.recover_source(x).cpu().numpy()
+    fr = okkt.source(p, U)
+    assert np.linalg.norm(f - fr) <= 1e-5 * np.linalg.norm(fr)
+
+
+def test_zero_rhs_gives_zero_solution_and_nan_is_reported(api):
+    w = W.random_small(7, cells=(3, 3, 3), M=3)
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, (1, 1, 1, 1), 0, 64)
+    b = prob.zeros()
+    x, st, its, rel = api.gmres_solve(prob, b, ras=ras)
+    assert st == 0 and its == 0 and torch.count_nonzero(x).item() == 0
+    b[5] = float("nan")
+    from paper_1508_06103_gb300._lib import KktError
+    with pytest.raises(KktError):
+        api.gmres_solve(prob, b, ras=ras)
+
+
+def test_maxit_exhaustion_reports_not_converged(api):
+    w = W.random_small(8, cells=(4, 3, 3), M=4)
+    prob = api.Problem.from_workload(w)
+    b = _dev(W.random_vector(prob.n, 1))
+    x, st, its, rel = api.gmres_solve(prob, b, restart=5, rtol=1e-12, maxit=7)
+    assert st == 1 and its == 7 and rel > 1e-12
