@@ -1,0 +1,480 @@
+#!/usr/bin/env python
+"""Benchmark: time to solve the space-time KKT system to 1e-8 on one GB300.
+
+Workload: the 32^3-cell x 64-step inverse source problem (35,937 nodes x 65
+levels x 3 unknowns = 7,007,715 unknowns), two moving sources, 125 sensors,
+1% noise, a(x) from a seeded smooth field, v = (1,1,0) sin(pi z), Dirichlet on
+x = 0; two-level space-time RAS with 4x4x4x4 subdomains, overlap 2, ILU(0)
+local solves; coarse mesh 16^3 x 32 with overlap 1 and a 4-step coarse GMRES
+at tolerance 0.1; FGMRES(30) to a true relative residual of 1e-8, zero
+initial guess.
+
+One step = one full solve from observations to recovered source, i.e. every
+step of the hot path: right-hand side from the observations, refactorisation
+of the fine and coarse subdomain ILU(0) factors, the preconditioned FGMRES
+solve (KKT matvecs, RAS gather/solve/scatter, restriction, coarse GMRES,
+interpolation, two-level combination, CGS2 Arnoldi, true residual) and the
+extraction of the source.  The headline `value` is the mixed form (FP32
+subdomain and coarse factors, FP64 Krylov); the plain FP64 form is timed on
+the same GPU and reported beside it.
+
+Multi-GPU: the path does not shard across GPUs here; N ranks run N
+independent replicas (weak scaling, no collective on the data path; one
+barrier and a max-reduction of the elapsed time only).
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload and extrapolates to one solve (the sample is described in the
+output line).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KKT solve s to 1e-8 rel. residual (mixed vs FP64) at 32^3x64; matvec HBM GB/s"
+UNIT = "s"
+OBS_FILE = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64.txt")
+# Two-level FGMRES(30) iterations of this workload to 1e-8, as the GPU solve
+# measures them; the oracle runs the same algorithm, so its extrapolated solve
+# time uses the same count.
+ORACLE_ITERATIONS = 23
+FALLBACK_HBM_GBS = 6800.0
+
+
+def config_dict(w, extra=None):
+    d = {
+        "workload": "inverse source KKT, 32^3 cells x 64 steps, 7,007,715 unknowns",
+        "grid_cells": list(w.cells), "steps": w.M, "unknowns": w.unknowns, "sensors": len(w.sensor_xyz),
+        "subdomains": list(w.nsub), "overlap": w.overlap, "local_solver": "ILU(0)",
+        "coarse": list(w.coarse_cells) + [w.coarse_M], "coarse_overlap": w.coarse_overlap,
+        "coarse_gmres": {"rtol": w.coarse_rtol, "maxit": w.coarse_maxit},
+        "outer": f"FGMRES({w.restart}) rtol {w.rtol}", "factor_precision": "fp32 (mixed form)",
+        "l2": "no flush needed: each step streams > 9 GB of factors (L2 129 MB)",
+        "parallelism": "replicas",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample(iterations: int, budget_rows: int = 15000):
+    """Time the oracle's pieces on the 32^3 x 64 workload and extrapolate one solve.
+
+    Sample: one level-wise FP64 KKT matvec; the ILU(0) factorisation and the
+    triangular solve of the leading `budget_rows` rows of one interior fine
+    subdomain and of one coarse subdomain (their per-row costs times the
+    rows of all subdomains); the CGS2 vector work from numpy dot products.
+    """
+    import numpy as np
+
+    from oracle import kkt, schwarz
+    from paper_1508_06103_gb300 import workloads as W
+
+    w = W.mid()
+    t_all = time.time()
+    p = kkt.Problem.from_workload(w)
+    x = np.random.default_rng(0).standard_normal(p.n)
+    t = time.time()
+    kkt.apply(p, x)
+    t_mv = time.time() - t
+    t = time.time()
+    for _ in range(4):
+        float(x @ x)
+    t_dot = (time.time() - t) / 4
+
+    def box_costs(pp, nsub, overlap, rows):
+        bxs = schwarz.boxes(pp, nsub, overlap)
+        # an interior box (index of part 1 along every axis)
+        k = 1 + nsub[0] * (1 + nsub[1] * (1 + nsub[2] * 1))
+        b = bxs[min(k, len(bxs) - 1)]
+        nodes, levels = schwarz.box_nodes_levels(pp, b)
+        t0 = time.time()
+        A = schwarz.kkt.assemble_box(pp, nodes, levels)
+        idx, _ = schwarz.box_unknowns(pp, b)
+        rows = min(rows, A.shape[0])
+        pat = schwarz.local_pattern(pp, idx, rows=rows)
+        ilu = schwarz.ILU0(A, pat, rows=rows)
+        t_fac = time.time() - t0
+        t0 = time.time()
+        ilu.solve(np.ones(rows))
+        t_sol = time.time() - t0
+        total_rows = sum(3 * int(np.prod(bb.shape())) for bb in bxs)
+        return t_fac / rows * total_rows, t_sol / rows * total_rows, rows
+
+    fac_f, sol_f, rows_f = box_costs(p, w.nsub, w.overlap, budget_rows)
+    pc = schwarz.coarse_problem(p, w.coarse_cells, w.coarse_M)
+    fac_c, sol_c, rows_c = box_costs(pc, w.nsub, w.coarse_overlap, budget_rows // 2)
+    t = time.time()
+    kkt.apply(pc, np.ones(pc.n))
+    t_mv_c = time.time() - t
+    per_iter = (sol_f + 2 * t_mv + w.coarse_maxit * (sol_c + t_mv_c + 4 * 3 * t_dot / 14)
+                + np.mean([4 * (j + 1) + 2 for j in range(min(iterations, w.restart))]) * t_dot)
+    est = fac_f + fac_c + iterations * per_iter
+    sample = (f"oracle (numpy/scipy, FP64, single-threaded Python loops) on the 32^3x64 workload: one level-wise "
+              f"KKT matvec ({t_mv:.2f} s), ILU(0) factor+solve of the leading {rows_f} rows of an interior fine "
+              f"subdomain and {rows_c} rows of a coarse one, numpy dots for CGS2; extrapolated to all subdomain "
+              f"rows and {iterations} FGMRES iterations; sample wall {time.time() - t_all:.1f} s")
+    return est, sample
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1508_06103_gb300 import workloads as W
+
+    w = W.mid()
+    vals = []
+    sample = ""
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; warm-up steps are not repeated
+    t0 = time.time()
+    for _ in range(args.steps):
+        v, sample = oracle_sample(ORACLE_ITERATIONS, budget_rows=15000)
+        vals.append(v)
+    wall = time.time() - t0
+    value = float(sorted(vals)[len(vals) // 2])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, {"factor_precision": "fp64 (oracle)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "sample_wall_s": wall,
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    if rank == 0 or world == 1:
+        build.build()
+    barrier()
+    w = W.mid()
+    cobs_np = np.loadtxt(OBS_FILE, ndmin=2)
+    assert cobs_np.shape == (w.M + 1, len(w.sensor_xyz)), cobs_np.shape
+    cobs_host = torch.from_numpy(cobs_np).pin_memory()
+    cobs = cobs_host.cuda()
+    prob = api.Problem.from_workload(w)
+    stream = torch.cuda.current_stream()
+    b, x = prob.zeros(), prob.zeros()
+    f = torch.empty(prob.levels * prob.N, dtype=torch.float64, device="cuda")
+    f_host = torch.empty(prob.levels * prob.N, dtype=torch.float64).pin_memory()
+
+    def make(prec):
+        ras = api.RAS(prob, w.nsub, w.overlap, prec)
+        co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, w.coarse_overlap, w.coarse_rtol, w.coarse_maxit,
+                        prec)
+        return ras, co
+
+    last = {}
+
+    def step(ras, co, obs):
+        prob.rhs(obs, out=b)
+        ras.refactor()
+        co.refactor()
+        x.zero_()
+        _, st, its, rel = api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=w.restart, rtol=w.rtol,
+                                          maxit=3000)
+        prob.recover_source(x, out=f)
+        last.update(status=st, iters=its, relres=rel)
+
+    def timed(fn, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- mixed form: the headline -----------------------------------------
+    ras, co = make(32)
+    for _ in range(args.warmup):
+        step(ras, co, cobs)
+    launches0 = api.launch_count()
+    api.timing_reset(prob, ras)
+    api.timing_enable(True)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: step(ras, co, cobs), args.steps)
+    api.timing_enable(False)
+    launches = (api.launch_count() - launches0) // args.steps
+    ras_ms, ras_n = ras.timing()
+    mv_ms, mv_n = api.matvec_timing(prob)
+    mixed = dict(last)
+    info = ras.info()
+    # end-to-end through the public API with host buffers: H2D observations, D2H source
+    def e2e_step():
+        obs = cobs_host.to("cuda", non_blocking=True)
+        step(ras, co, obs)
+        f_host.copy_(f, non_blocking=True)
+
+    e2e_ms = timed(e2e_step, max(1, args.steps // 2))
+
+    # ---- plain FP64 form on the same GPU -----------------------------------
+    del ras, co
+    torch.cuda.synchronize()
+    ras64, co64 = make(64)
+    step(ras64, co64, cobs)
+    fp64_ms = timed(lambda: step(ras64, co64, cobs), args.fp64_steps)
+    fp64 = dict(last)
+    del ras64, co64
+
+    # ---- the KKT matvec on its own (FP64 and FP32) --------------------------
+    xm = torch.randn(prob.n, dtype=torch.float64, device="cuda")
+    ym = torch.empty_like(xm)
+    xs, ys = xm.float(), torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    reps = 20
+    mv64_ms = timed(lambda: prob.apply(xm, ym), reps)
+    mv32_ms = timed(lambda: prob.apply(xs, ys), reps)
+    coef_bytes = 4 * 27 * prob.N
+    mv64_bytes = prob.n * 16 + coef_bytes * 8
+    mv32_bytes = prob.n * 8 + coef_bytes * 4
+
+    peak, peak_kind = measured_peaks()
+    # dominant kernel: the fine subdomain solve (ras_solve<float>)
+    ras_avg_ms = ras_ms / max(ras_n, 1)
+    ras_bytes = info["factor_values"] * info["value_bytes"] + info["points"] * 3 * 8 + prob.n * 8
+    achieved = ras_bytes / (ras_avg_ms * 1e-3) / 1e9
+    traffic = read_traffic("ras_solve")
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w),
+        "solves_per_s": world * 1e3 / ms,
+        "iterations": mixed.get("iters"), "true_relres": mixed.get("relres"), "status": mixed.get("status"),
+        "fp64_form": {"s_per_solve": fp64_ms / 1e3, "iterations": fp64.get("iters"),
+                      "true_relres": fp64.get("relres"), "steps": args.fp64_steps},
+        "mixed_speedup_vs_fp64": fp64_ms / ms,
+        "matvec": {"fp64_gbs": mv64_bytes / (mv64_ms * 1e-3) / 1e9, "fp64_us": mv64_ms * 1e3,
+                   "fp32_gbs": mv32_bytes / (mv32_ms * 1e-3) / 1e9, "fp32_us": mv32_ms * 1e3,
+                   "fp64_frac": mv64_bytes / (mv64_ms * 1e-3) / 1e9 / peak,
+                   "fp32_frac": mv32_bytes / (mv32_ms * 1e-3) / 1e9 / peak,
+                   "bytes_fp64": mv64_bytes, "bytes_fp32": mv32_bytes},
+        "roofline": {"kernel": "ras_solve<float> (fine subdomain ILU(0) solve, all 256 boxes)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "alg_bytes_per_launch": ras_bytes,
+                     "avg_launch_ms": ras_avg_ms, "launches_per_step": ras_n / args.steps,
+                     "share_of_step": ras_ms / args.steps / ms},
+        "outer_matvec": {"avg_launch_ms": mv_ms / max(mv_n, 1), "launches_per_step": mv_n / args.steps},
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_ms / 1e3, "unit": UNIT, "h2d_bytes_per_step": cobs_np.size * 8,
+                "d2h_bytes_per_step": prob.levels * prob.N * 8},
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        est, sample = oracle_sample(int(mixed.get("iters") or ORACLE_ITERATIONS))
+        line["cpu_baseline"] = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(line))
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries, if any.
+
+    A summary states it on one line as `traffic <kernel>: <bytes per launch>`.
+    """
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        for ln in open(os.path.join(pdir, name)):
+            if ln.strip().startswith(f"traffic {kernel}:"):
+                try:
+                    return float(ln.split(":", 1)[1].split()[0])
+                except ValueError:
+                    return None
+    return None
+
+
+def kernel_arm(args):
+    """One kernel on a member of the same problem family (for profiling and sweeps).
+
+    --kernel ras     : fine one-level RAS apply (subdomain solve), FP32 factors
+    --kernel matvec  : FP64 and FP32 KKT matvecs
+    """
+    import torch
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    build.build()
+    c, M = args.cells, args.levels
+    w = W.mid(cells=(c, c, c), M=M, coarse_cells=None, coarse_M=None)
+    prob = api.Problem.from_workload(w)
+    x = torch.randn(prob.n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    out = {"kernel": args.kernel, "cells": c, "levels": M, "unknowns": prob.n}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.kernel == "ras":
+        ras = api.RAS(prob, w.nsub, w.overlap, args.prec)
+        ras.apply(x, y)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.reps):
+            ras.apply(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        info = ras.info()
+        ms = e0.elapsed_time(e1) / args.reps
+        by = info["factor_values"] * info["value_bytes"] + info["points"] * 24 + prob.n * 8
+        out.update(info, ms=ms, alg_bytes=by, gbs=by / ms / 1e6)
+    else:
+        xs, ys = x.float(), torch.empty(prob.n, dtype=torch.float32, device="cuda")
+        for name, (a, b_) in (("fp64", (x, y)), ("fp32", (xs, ys))):
+            prob.apply(a, b_)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.reps):
+                prob.apply(a, b_)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            by = prob.n * (16 if name == "fp64" else 8) + 4 * 27 * prob.N * (8 if name == "fp64" else 4)
+            out[name] = {"ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["ras", "matvec"], default=None,
+                    help="time one kernel on a member of the workload family instead of the full solve")
+    ap.add_argument("--cells", type=int, default=32)
+    ap.add_argument("--levels", type=int, default=64)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--prec", type=int, default=32)
+    args = ap.parse_args()
+    if args.kernel:
+        kernel_arm(args)
+    elif args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -139,6 +139,14 @@ kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, 
                      ras_precond** out);
 
 /*
+ * ras_info -- sizes of a preconditioner: boxes, points of all extended boxes
+ *   (with overlap), stored factor values and bytes per value.  Any output may
+ *   be NULL.
+ */
+kkt_status ras_info(const ras_precond* m, int* nbox, long long* points, long long* factor_values,
+                    int* value_bytes);
+
+/*
  * ras_apply -- z = sum_ij (R^0_ij)^T M_ij^{-1} R^delta_ij r (restricted prolongation,
  *   Cai-Sarkis form cited in Sec. 3.2); all boxes in one launch.  r, z FP64, must
  *   not overlap.
@@ -182,6 +190,36 @@ kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const double* x, 
 kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* c, const double* b, double* x,
                        int restart, double rtol, int maxit, int flexible, int* iters,
                        double* true_relres, void* stream);
+
+/*
+ * ras_refactor -- recompute the ILU(0) factors of an existing preconditioner in
+ *   place from its problem's current coefficients (the factorisation step of
+ *   ras_setup without any allocation).  Enqueued on `stream`, then synchronises
+ *   it to report a zero pivot.  Errors: ARG, CUDA, ZERO_PIVOT.
+ */
+kkt_status ras_refactor(ras_precond* m, void* stream);
+
+/* coarse_refactor -- ras_refactor of the coarse level's one-level RAS. */
+kkt_status coarse_refactor(coarse_level* c, void* stream);
+
+/*
+ * Instrumentation (no effect on results).
+ * kkt_launch_count  -- number of CUDA kernels the library has launched since it
+ *                      was loaded (all handles, all threads).
+ * kkt_timing_enable -- 1: bracket every launch of the outer KKT matvec and of the
+ *                      RAS subdomain-solve kernel with CUDA events on the launch
+ *                      stream; 0: stop.  Returns the previous setting.
+ * kkt_timing_read   -- accumulated event time (ms) and launch count of the FP64
+ *                      matvecs issued by the solver on problem p (synchronises
+ *                      on the recorded events).
+ * ras_timing_read   -- the same for the subdomain-solve launches of RAS m.
+ * kkt_timing_reset  -- clear the accumulators of p and m (either may be NULL).
+ */
+long long kkt_launch_count(void);
+int kkt_timing_enable(int on);
+kkt_status kkt_timing_read(kkt_problem* p, double* total_ms, long long* launches);
+kkt_status ras_timing_read(ras_precond* m, double* total_ms, long long* launches);
+kkt_status kkt_timing_reset(kkt_problem* p, ras_precond* m);
 
 /*
  * recover_source -- f of the point-block vector U as an (M+1) x N array

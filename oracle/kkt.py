@@ -108,47 +108,63 @@ def _identity_rows(Mblk: sp.csr_matrix, rows_mask: np.ndarray, diag: bool) -> sp
     return out.tocsr()
 
 
-def assemble_field_major(p: Problem) -> sp.csr_matrix:
-    """F_h in the Appendix's field-major ordering (C^0..C^M, G^0..G^M, f^0..f^M)."""
-    N, M, L = p.N, p.M, p.L
+def assemble_field_major(p: Problem, nodes=None, levels=None) -> sp.csr_matrix:
+    """F_h in the Appendix's field-major ordering (C^0..C^M, G^0..G^M, f^0..f^M).
+
+    With `nodes` (sorted node ids) and `levels` (a contiguous range of levels)
+    only the principal submatrix on those nodes and levels is built, in the
+    same field-major order restricted to them (used for subdomain matrices).
+    """
+    M = p.M
     th, tau = p.theta, p.tau
-    A1, A2, B1, B2 = _state_blocks(p)
+    nodes = np.arange(p.N) if nodes is None else np.asarray(nodes)
+    levels = list(range(p.L)) if levels is None else list(levels)
+    N, L = len(nodes), len(levels)
+    sub = lambda A: A[nodes][:, nodes].tocsr()
+    A1, A2, B1, B2 = (sub(X) for X in _state_blocks(p))
+    Bs, Ks = sub(p.B), sub(p.K)
     I = sp.identity(N, format="csr")
     Z = None
-    D = p.dirichlet
-    B3 = sp.diags(np.where(D, 0.0, p.s))
+    D = p.dirichlet[nodes]
+    B3 = sp.diags(np.where(p.dirichlet, 0.0, p.s)[nodes])
     Mt = p.Mt.toarray()
     Lt = p.Lt.toarray()
+    col = {n: k for k, n in enumerate(levels)}      # level -> block column within a field
     blocks = [[Z] * (3 * L) for _ in range(3 * L)]
+
+    def put(r, field, m, blk):
+        if m in col:
+            blocks[r][field * L + col[m]] = blk
+
     # C rows
-    for n in range(L):
-        r = n
+    for k, n in enumerate(levels):
+        r = k
         if n == 0:
-            blocks[r][0] = I
+            put(r, 0, 0, I)
             continue
-        blocks[r][n - 1] = _identity_rows(A2, D, False)
-        blocks[r][n] = _identity_rows(A1, D, True)
-        blocks[r][2 * L + n - 1] = _identity_rows(-(1.0 - th) * tau * p.B, D, False)
-        blocks[r][2 * L + n] = _identity_rows(-th * tau * p.B, D, False)
+        put(r, 0, n - 1, _identity_rows(A2, D, False))
+        put(r, 0, n, _identity_rows(A1, D, True))
+        put(r, 2, n - 1, _identity_rows(-(1.0 - th) * tau * Bs, D, False))
+        put(r, 2, n, _identity_rows(-th * tau * Bs, D, False))
     # G rows
-    for n in range(L):
-        r = L + n
+    for k, n in enumerate(levels):
+        r = L + k
         if n == M:
-            blocks[r][L + M] = I
+            put(r, 1, M, I)
             continue
-        blocks[r][L + n] = _identity_rows(B1, D, True)
-        blocks[r][L + n + 1] = _identity_rows(B2, D, False)
-        blocks[r][n] = (1.0 - th) * tau * B3
-        blocks[r][n + 1] = th * tau * B3
+        put(r, 1, n, _identity_rows(B1, D, True))
+        put(r, 1, n + 1, _identity_rows(B2, D, False))
+        put(r, 0, n, (1.0 - th) * tau * B3)
+        put(r, 0, n + 1, th * tau * B3)
     # f rows
-    for n in range(L):
-        r = 2 * L + n
+    for k, n in enumerate(levels):
+        r = 2 * L + k
         for m in range(max(0, n - 1), min(M, n + 1) + 1):
-            blocks[r][L + m] = -Mt[n, m] * p.B
-            blocks[r][2 * L + m] = p.beta1 * Lt[n, m] * p.B + p.beta2 * Mt[n, m] * p.K
-    # every block row needs a defined shape for bmat
+            put(r, 1, m, -Mt[n, m] * Bs)
+            put(r, 2, m, p.beta1 * Lt[n, m] * Bs + p.beta2 * Mt[n, m] * Ks)
+    # every block row and column needs a defined shape for bmat
     for r in range(3 * L):
-        if all(b is None for b in blocks[r]):
+        if blocks[r][r] is None:
             blocks[r][r] = sp.csr_matrix((N, N))
     return sp.bmat(blocks, format="csr")
 
@@ -158,6 +174,20 @@ def assemble(p: Problem) -> sp.csr_matrix:
     Ff = assemble_field_major(p)
     perm = p.field_to_pointblock()
     Pi = sp.csr_matrix((np.ones(p.n), (perm, np.arange(p.n))), shape=(p.n, p.n))
+    return (Pi @ Ff @ Pi.T).tocsr()
+
+
+def assemble_box(p: Problem, nodes, levels) -> sp.csr_matrix:
+    """Principal submatrix of F_h on the unknowns of `nodes` x `levels`, in the local
+    point-block order (level slowest, then the given node order, then component)."""
+    Ff = assemble_field_major(p, nodes, levels)
+    N, L = len(nodes), len(levels)
+    n = 3 * N * L
+    k = np.arange(n)
+    c, rem = np.divmod(k, N * L)
+    t, j = np.divmod(rem, N)
+    perm = (t * N + j) * 3 + c
+    Pi = sp.csr_matrix((np.ones(n), (perm, k)), shape=(n, n))
     return (Pi @ Ff @ Pi.T).tocsr()
 
 

@@ -77,6 +77,14 @@ def boxes(p: kkt.Problem, nsub: Sequence[int], overlap: int) -> List[Box]:
     return out
 
 
+def box_nodes_levels(p: kkt.Problem, b: Box):
+    """Node ids (x fastest) and level range of a box's extended set."""
+    nx, ny, nz = p.nodes
+    (x0, x1), (y0, y1), (z0, z1), (t0, t1) = b.ext
+    z, y, x = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+    return (x + nx * (y + ny * z)).ravel(), range(t0, t1)
+
+
 def box_unknowns(p: kkt.Problem, b: Box):
     """Global point-block indices of the box's unknowns in local lexicographic
     order (t slowest, then z, y, x, then component), and a mask of the owned ones."""
@@ -101,8 +109,10 @@ class ILU0:
     The strictly lower part is L (unit diagonal), the rest is U.
     """
 
-    def __init__(self, Aloc: sp.csr_matrix, pattern: List[np.ndarray]):
-        n = Aloc.shape[0]
+    def __init__(self, Aloc: sp.csr_matrix, pattern: List[np.ndarray], rows: int | None = None):
+        """rows: factor only the leading rows x rows block (its ILU(0) is the
+        leading part of the full one, as row i only uses rows k < i)."""
+        n = Aloc.shape[0] if rows is None else int(rows)
         Aloc = Aloc.tocsr()
         self.n = n
         self.L: List[dict] = []
@@ -111,7 +121,7 @@ class ILU0:
         for i in range(n):
             vals = dict(zip(Aloc.indices[Aloc.indptr[i]:Aloc.indptr[i + 1]].tolist(),
                             Aloc.data[Aloc.indptr[i]:Aloc.indptr[i + 1]].tolist()))
-            cols = sorted(int(c) for c in pattern[i])
+            cols = sorted(int(c) for c in pattern[i] if c < n)
             row = {c: vals.get(c, 0.0) for c in cols}
             for k in cols:
                 if k >= i:
@@ -153,11 +163,12 @@ class ExactLU:
         return self.lu.solve(np.asarray(r, dtype=np.float64))
 
 
-def local_pattern(p: kkt.Problem, idx: np.ndarray) -> List[np.ndarray]:
-    """Structural pattern of F_h restricted to the unknowns idx (local numbering)."""
+def local_pattern(p: kkt.Problem, idx: np.ndarray, rows: int | None = None) -> List[np.ndarray]:
+    """Structural pattern of F_h restricted to the unknowns idx (local numbering);
+    with `rows`, only the first rows rows."""
     pos = {int(g): k for k, g in enumerate(idx)}
     out = []
-    for g in idx:
+    for g in (idx if rows is None else idx[:rows]):
         c = int(g % 3)
         pt = int(g // 3)
         n, j = divmod(pt, p.N)

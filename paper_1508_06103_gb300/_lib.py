@@ -43,6 +43,15 @@ SIGNATURES = {
     "gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                               C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]),
     "recover_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ras_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ras_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                           C.POINTER(C.c_int)]),
+    "coarse_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "kkt_launch_count": (C.c_longlong, []),
+    "kkt_timing_enable": (C.c_int, [C.c_int]),
+    "kkt_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "ras_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "kkt_timing_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
     "kkt_destroy": (None, [C.c_void_p]),
     "ras_destroy": (None, [C.c_void_p]),
     "coarse_destroy": (None, [C.c_void_p]),

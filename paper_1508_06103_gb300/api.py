@@ -119,6 +119,21 @@ class RAS:
         check(self._lib.ras_apply(self.h, _ptr(r), _ptr(z), _stream(stream)), "ras_apply")
         return z
 
+    def refactor(self, stream=None) -> None:
+        check(self._lib.ras_refactor(self.h, _stream(stream)), "ras_refactor")
+
+    def info(self):
+        """dict(nbox, points, factor_values, value_bytes)."""
+        nb, pts, fv, vb = C.c_int(), C.c_longlong(), C.c_longlong(), C.c_int()
+        check(self._lib.ras_info(self.h, C.byref(nb), C.byref(pts), C.byref(fv), C.byref(vb)), "ras_info")
+        return dict(nbox=nb.value, points=pts.value, factor_values=fv.value, value_bytes=vb.value)
+
+    def timing(self):
+        """(total ms, launches) of the subdomain-solve kernel since the last reset."""
+        ms, n = C.c_double(), C.c_longlong()
+        check(self._lib.ras_timing_read(self.h, C.byref(ms), C.byref(n)), "ras_timing_read")
+        return ms.value, n.value
+
     def close(self):
         if self.h is not None and self.h.value:
             self._lib.ras_destroy(self.h)
@@ -150,6 +165,9 @@ class Coarse:
         check(self._lib.two_level_apply(self.h, fine.h, _ptr(x), _ptr(z), _stream(stream)), "two_level_apply")
         return z
 
+    def refactor(self, stream=None) -> None:
+        check(self._lib.coarse_refactor(self.h, _stream(stream)), "coarse_refactor")
+
     def close(self):
         if self.h is not None and self.h.value:
             self._lib.coarse_destroy(self.h)
@@ -160,6 +178,26 @@ class Coarse:
             self.close()
         except Exception:
             pass
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(_lib.load().kkt_launch_count())
+
+
+def timing_enable(on: bool) -> bool:
+    return bool(_lib.load().kkt_timing_enable(int(on)))
+
+
+def matvec_timing(prob: Problem):
+    """(total ms, launches) of the solver's FP64 matvecs on prob since the last reset."""
+    ms, n = C.c_double(), C.c_longlong()
+    check(_lib.load().kkt_timing_read(prob.h, C.byref(ms), C.byref(n)), "kkt_timing_read")
+    return ms.value, n.value
+
+
+def timing_reset(prob: Optional[Problem] = None, ras: Optional["RAS"] = None) -> None:
+    _lib.load().kkt_timing_reset(prob.h if prob else None, ras.h if ras else None)
 
 
 def gmres_solve(prob: Problem, b: torch.Tensor, x: Optional[torch.Tensor] = None, ras: Optional[RAS] = None,

@@ -3,8 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "stkkt.h"
@@ -25,6 +27,29 @@ void set_error(const std::string& msg);
     kkt_status st_ = (call);          \
     if (st_ < 0) return st_;          \
   } while (0)
+
+// Count of kernel launches made by the library (kkt_launch_count).
+extern std::atomic<long long> g_kernel_launches;
+#define KKT_COUNT(n) g_kernel_launches.fetch_add((n), std::memory_order_relaxed)
+
+// CUDA-event timing of selected launches (kkt_timing_enable / *_timing_read).
+extern std::atomic<int> g_timing_on;
+struct TimingLog {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double total_ms = 0.0;
+  long long count = 0;
+  void drain();            // synchronise on pending events and accumulate
+  void reset();
+  ~TimingLog();
+};
+// Records an event pair around the launches issued in its scope when timing is on.
+struct TimedScope {
+  TimingLog* log;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  TimedScope(TimingLog* l, cudaStream_t st);
+  ~TimedScope();
+};
 
 // 27-point stencil offsets: d = (dx+1) + 3 (dy+1) + 9 (dz+1), centre d = 13.
 constexpr int kStencil = 27;
@@ -74,6 +99,7 @@ struct kkt_problem {
   int* sens_idx = nullptr;                  // sensor ids ordered by node
   int nsens = 0;
   GmresWork* ws = nullptr;                  // outer Krylov workspace (lazily allocated)
+  TimingLog mv_timing;                      // outer FP64 matvec launches
   DevProblem dev() const;
 };
 

@@ -101,6 +101,7 @@ kkt_status multidot(const double* V, long long ldv, int m, const double* w, long
   dim3 g(kDotBlocks, m);
   multidot_partial<<<g, kDotThreads, 0, s>>>(V, ldv, w, n, part);
   multidot_final<<<m, 256, 0, s>>>(part, kDotBlocks, out, 0);
+  KKT_COUNT(2);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
@@ -119,6 +120,7 @@ kkt_status vec_zero(double* y, long long n, cudaStream_t s) {
 
 kkt_status vec_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s) {
   axpby_kernel<<<kVecBlocks, 256, 0, s>>>(y, a, x, b, n);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
@@ -211,6 +213,7 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     scale_kernel<<<kVecBlocks, 256, 0, s>>>(ws.V, ws.r, 1.0 / beta, n);
+    KKT_COUNT(1);
     KKT_TRY_CUDA(cudaGetLastError());
     int k = 0;
     bool stop = false;
@@ -226,6 +229,7 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
       KKT_TRY(multidot(ws.V, n, j + 1, ws.w, n, ws.part, h2dev, s));
       multi_axpy<<<kVecBlocks, 256, 0, s>>>(ws.w, ws.V, n, h2dev, j + 1, n);
       add_kernel<<<1, 64, 0, s>>>(hdev, h2dev, j + 1);
+      KKT_COUNT(3);
       KKT_TRY_CUDA(cudaGetLastError());
       KKT_TRY(multidot(ws.w, 0, 1, ws.w, n, ws.part, hdev + j + 1, s));
       KKT_TRY_CUDA(cudaMemcpyAsync(hh, hdev, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -261,6 +265,7 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
         break;
       }
       scale_kernel<<<kVecBlocks, 256, 0, s>>>(ws.V + (size_t)(j + 1) * n, ws.w, 1.0 / hn, n);
+      KKT_COUNT(1);
       KKT_TRY_CUDA(cudaGetLastError());
     }
     for (int i = k - 1; i >= 0; --i) {
@@ -271,10 +276,12 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
     KKT_TRY_CUDA(cudaMemcpyAsync(ydev, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
     if (ws.flexible) {
       multi_update<<<kVecBlocks, 256, 0, s>>>(x, ws.Z, n, ydev, k, n);
+      KKT_COUNT(1);
     } else {
       // x += M^{-1} (V y): form V y in w, precondition into r
       KKT_TRY(vec_zero(ws.w, n, s));
       multi_update<<<kVecBlocks, 256, 0, s>>>(ws.w, ws.V, n, ydev, k, n);
+      KKT_COUNT(1);
       if (M) KKT_TRY(M->apply(ws.w, ws.r, s));
       else KKT_TRY(vec_copy(ws.r, ws.w, n, s));
       KKT_TRY(vec_axpby(x, 1.0, ws.r, 1.0, n, s));

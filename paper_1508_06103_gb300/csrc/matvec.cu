@@ -121,18 +121,21 @@ __global__ void sub_f2d(const double* __restrict__ b, const float* __restrict__ 
 
 kkt_status launch_matvec64(const DevProblem& p, const double* x, double* y, cudaStream_t s) {
   matvec_kernel<double><<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p, x, y, nullptr);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
 
 kkt_status launch_matvec32(const DevProblem& p, const float* x, float* y, cudaStream_t s) {
   matvec_kernel<float><<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p, x, y, nullptr);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
 
 kkt_status launch_residual(const DevProblem& p, const double* b, const double* x, double* r, cudaStream_t s) {
   matvec_kernel<double><<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p, x, r, b);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
@@ -144,6 +147,7 @@ kkt_status launch_residual32(const DevProblem& p, const double* b, const double*
   d2f<<<1216, 256, 0, s>>>(x, x32, n);
   matvec_kernel<float><<<(unsigned)((p.P + 255) / 256), 256, 0, s>>>(p, x32, y32, nullptr);
   sub_f2d<<<1216, 256, 0, s>>>(b, y32, r, n);
+  KKT_COUNT(3);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }

@@ -23,6 +23,64 @@
 #include "internal.cuh"
 
 static thread_local std::string g_last_error;
+std::atomic<long long> g_kernel_launches{0};
+std::atomic<int> g_timing_on{0};
+
+void TimingLog::drain() {
+  for (auto& ev : pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(ev.second) == cudaSuccess && cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+      total_ms += ms;
+      ++count;
+    }
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  pending.clear();
+}
+
+void TimingLog::reset() {
+  drain();
+  total_ms = 0.0;
+  count = 0;
+}
+
+TimingLog::~TimingLog() {
+  for (auto& ev : pending) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+}
+
+TimedScope::TimedScope(TimingLog* l, cudaStream_t st) : log(l), s(st) {
+  if (g_timing_on.load() && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
+  else e0 = nullptr;
+}
+
+TimedScope::~TimedScope() {
+  if (!e0) return;
+  cudaEvent_t e1;
+  if (cudaEventCreate(&e1) == cudaSuccess) {
+    cudaEventRecord(e1, s);
+    log->pending.emplace_back(e0, e1);
+  } else {
+    cudaEventDestroy(e0);
+  }
+}
+
+extern "C" long long kkt_launch_count(void) { return g_kernel_launches.load(); }
+extern "C" int kkt_timing_enable(int on) { return g_timing_on.exchange(on ? 1 : 0); }
+
+extern "C" kkt_status kkt_timing_read(kkt_problem* p, double* total_ms, long long* launches) {
+  if (!p) {
+    set_error("kkt_timing_read: null problem");
+    return KKT_ERR_ARG;
+  }
+  p->mv_timing.drain();
+  if (total_ms) *total_ms = p->mv_timing.total_ms;
+  if (launches) *launches = p->mv_timing.count;
+  return KKT_OK;
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -229,6 +287,7 @@ kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_
     assemble_stencils<<<(unsigned)((N + 127) / 128), 128>>>(geo, d_a, d_v, p->coef64, p->coef64 + c,
                                                             p->coef64 + 2 * c, p->coef64 + 3 * c);
     to_float<<<1024, 256>>>(p->coef64, p->coef32, ncoef);
+    KKT_COUNT(2);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -268,6 +327,7 @@ extern "C" kkt_status kkt_rhs(kkt_problem* p, const double* c_obs, const double*
   }
   const unsigned blocks = (unsigned)((p->P + 255) / 256);
   rhs_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(p->dev(), c_obs, p->nsens, c0, p->sens_ptr, p->sens_idx, b);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
@@ -278,6 +338,7 @@ extern "C" kkt_status recover_source(kkt_problem* p, const double* U, double* f,
     return KKT_ERR_ARG;
   }
   source_kernel<<<(unsigned)((p->P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(U, f, p->P);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }

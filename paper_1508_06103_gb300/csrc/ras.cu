@@ -15,8 +15,15 @@
 // (time slowest, then z, y, x, then component).  Every point of a box stores
 // 108 + 56 + 162 = 326 slot values, no column indices; slots whose column is
 // outside the box hold 0, which is the same as leaving them out of the
-// pattern.  Values are laid out [slot][point in wavefront order] per box so
-// that the threads working on one wavefront read consecutive addresses.
+// pattern.
+//
+// Layout in HBM.  The points of each wavefront are cut into chunks of at most
+// CH points (56 in FP32, 28 in FP64).  A chunk's values form one contiguous
+// block [slot rank][point of the chunk] with a row stride cp >= the chunk's
+// point count chosen so that the shared-memory reads of the solve are free of
+// bank conflicts; the L-slots of the three rows come first (175 ranks), then
+// the diagonal and U-slots (151 ranks).  The forward sweep therefore streams
+// one contiguous L block per chunk and the backward sweep one U block.
 //
 // Ordering and parallelism.  Points are processed in the natural
 // (lexicographic) order of the box; with this stencil every lower-triangular
@@ -31,9 +38,14 @@
 // The (row slot, column slot) pairs of the inner update are precomputed per
 // row type as tables of slot indices.
 //
-// Solve.  The local vector of each box has a ghost layer of zeros one point
-// wide in every direction, so the triangular sweeps need no bounds tests:
-// a slot whose column leaves the box reads 0 and has factor value 0.
+// Solve.  One CTA per box runs a two-stage pipeline over its chunks: thread 0
+// issues a TMA bulk copy (cp.async.bulk, completion on an mbarrier) of the
+// next chunk's L (or U) block into one of two shared-memory buffers while the
+// CTA computes the current chunk from the other.  The local vector of each box
+// has a ghost layer of zeros one point wide in every direction, so the
+// triangular sweeps need no bounds tests: a slot whose column leaves the box
+// reads 0 and has factor value 0.  Small boxes keep the local vector in shared
+// memory as well.
 
 #include <algorithm>
 #include <array>
@@ -111,13 +123,55 @@ const SlotTables& tables() {
 
 __constant__ int8_t c_dt[kSlots], c_dz[kSlots], c_dy[kSlots], c_dx[kSlots], c_comp[kSlots];
 __constant__ int c_base[3], c_count[3], c_diag[3];
+__constant__ short c_rank[kSlots];   // slot -> row of the chunk block
+
+// Slot ranges of the three row types (checked against the tables on the host).
+constexpr int kCBase = 0, kCDiag = 80, kCEnd = 108;
+constexpr int kGBase = 108, kGDiag = 122, kGEnd = 164;
+constexpr int kFBase = 164, kFDiag = 245, kFEnd = 326;
+constexpr int kLRanks = 175;        // L-slots of the three rows
+constexpr int kURanks = 151;        // diagonals and U-slots of the three rows
+constexpr int kMaxRow = 162;        // slots of the longest row (f)
+constexpr int kMaxUpd = 2320;       // factorisation updates of the longest row (f)
+constexpr int kMaxL = 81;           // L-slots of the longest row (f)
+
+// rank of slot s in a chunk block: L-slots of C, G, f, then diag+U of C, G, f
+int slot_rank(int s) {
+  if (s < kCDiag) return s;
+  if (s >= kGBase && s < kGDiag) return 80 + (s - kGBase);
+  if (s >= kFBase && s < kFDiag) return 94 + (s - kFBase);
+  if (s >= kCDiag && s < kCEnd) return kLRanks + (s - kCDiag);
+  if (s >= kGDiag && s < kGEnd) return kLRanks + 28 + (s - kGDiag);
+  return kLRanks + 70 + (s - kFDiag);
+}
+
+template <typename T>
+struct ChunkCfg;
+template <>
+struct ChunkCfg<float> {
+  static constexpr int CH = 56;       // points per chunk (4 lanes each: 7 full warps)
+  static constexpr int Q = 16, R = 8; // row stride cp = 8 (mod 16): conflict-free 4-lane reads
+  static constexpr int CHP = 56;      // largest row stride (that of a full chunk)
+};
+template <>
+struct ChunkCfg<double> {
+  static constexpr int CH = 32;       // 4 full warps
+  static constexpr int Q = 8, R = 4;  // cp = 4 (mod 8)
+  static constexpr int CHP = 36;
+};
+
+template <typename T>
+int chunk_stride(int n) {
+  const int Q = ChunkCfg<T>::Q, R = ChunkCfg<T>::R;
+  return n <= R ? R : R + ((n - R + Q - 1) / Q) * Q;
+}
 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
 
-// Matrix entry of F_h in row (point, type c) at slot s (global coordinates).
-__device__ double kkt_entry(const DevProblem& p, int c, int s, int j, int n, int jn, int d) {
+// Matrix entry of F_h in row (point, type c) at slot s; j node, n level.
+__device__ double kkt_entry(const DevProblem& p, int c, int s, int j, int n, int d) {
   const double tau = p.tau, th = p.theta, th1 = 1.0 - p.theta;
   const int dt = c_dt[s], cc = c_comp[s];
   const size_t ci = (size_t)d * p.N + j;
@@ -133,7 +187,6 @@ __device__ double kkt_entry(const DevProblem& p, int c, int s, int j, int n, int
     return (dt == 0 ? th1 : th) * tau * p.sens[j];
   }
   // f row: time mass / stiffness weights of the linear hats
-  const int m = n + dt;
   double mt, lt;
   if (dt == 0) {
     mt = (n > 0 ? tau / 3 : 0.0) + (n < p.M ? tau / 3 : 0.0);
@@ -142,23 +195,30 @@ __device__ double kkt_entry(const DevProblem& p, int c, int s, int j, int n, int
     mt = tau / 6;
     lt = -1.0 / tau;
   }
-  (void)m;
-  (void)jn;
   if (cc == 1) return -mt * p.B[ci];
   return p.beta1 * lt * p.B[ci] + p.beta2 * mt * p.K[ci];
+}
+
+// address of slot s of point q (wavefront order) inside the box's storage
+__device__ __forceinline__ long long slot_addr(const long long* __restrict__ qoff, const int* __restrict__ qcp,
+                                               int q, int s) {
+  return qoff[q] + (long long)c_rank[s] * qcp[q];
 }
 
 // Fill the slot values of every point of every box from the stencil coefficients.
 template <typename T>
 __global__ void gather_matrix(DevProblem p, const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
+                              const long long* __restrict__ qoff_g, const int* __restrict__ qcp_g,
                               T* __restrict__ F) {
   const BoxDesc bx = boxes[blockIdx.y];
   const long long P = bx.P;
   T* Fb = F + bx.foff;
+  const long long* qoff = qoff_g + bx.poff;
+  const int* qcp = qcp_g + bx.poff;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < P * kSlots;
        r += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(r / P);
-    const long long q = r - (long long)s * P;      // wavefront-order position
+    const int q = (int)(r / kSlots);
+    const int s = (int)(r - (long long)q * kSlots);
     const int lex = perm[bx.poff + q];
     const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
     const int kt = lex / (bx.lx * bx.ly * bx.lz);
@@ -169,108 +229,296 @@ __global__ void gather_matrix(DevProblem p, const BoxDesc* __restrict__ boxes, c
       const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, gt = bx.t0 + kt;
       const int j = gx + p.nx * (gy + p.ny * gz);
       const int d = (c_dx[s] + 1) + 3 * (c_dy[s] + 1) + 9 * (c_dz[s] + 1);
-      v = kkt_entry(p, c, s, j, gt, 0, d);
+      v = kkt_entry(p, c, s, j, gt, d);
     }
-    Fb[(size_t)s * P + q] = (T)v;
+    Fb[slot_addr(qoff, qcp, q, s)] = (T)v;
   }
 }
 
-// ILU(0) of every box: one CTA per box, wavefront by wavefront.
+// ---------------------------------------------------------------------------
+// ILU(0) factorisation: one CTA per box, one warp per point of a wavefront.
+// For each row the warp first gathers, in parallel, every value the IKJ
+// elimination of that row will read (the pivots u_kk and the U entries u_kj of
+// the rows k it eliminates with), then runs the sequential elimination on
+// shared memory with the updates of one pivot spread over the lanes.
+// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) ilu0_factor(const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
-                                                   const int* __restrict__ iperm, const int* __restrict__ lptr,
-                                                   const int* __restrict__ uptr, const short2* __restrict__ upd,
-                                                   T* __restrict__ F, int* __restrict__ status) {
+struct FactorSmem {
+  static size_t bytes(int warps, int nupd) {
+    return (size_t)nupd * sizeof(short2) + (kSlots + 1) * sizeof(int) + (size_t)nupd * sizeof(short) +
+           (size_t)warps * ((kMaxRow + kMaxUpd + kMaxL) * sizeof(T) + kMaxL * sizeof(int)) + 64;
+  }
+};
+
+template <typename T>
+__global__ void ilu0_factor(const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
+                            const int* __restrict__ iperm, const int* __restrict__ lptr,
+                            const long long* __restrict__ qoff_g, const int* __restrict__ qcp_g,
+                            const int* __restrict__ uptr_g, const short2* __restrict__ upd_g, int nupd,
+                            T* __restrict__ F, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* rowb = reinterpret_cast<T*>(smem) + (size_t)warp * (kMaxRow + kMaxUpd + kMaxL);
+  T* gath = rowb + kMaxRow;
+  T* piv = gath + kMaxUpd;
+  int* kqs0 = reinterpret_cast<int*>(reinterpret_cast<T*>(smem) + (size_t)nwarps * (kMaxRow + kMaxUpd + kMaxL));
+  int* kqs = kqs0 + warp * kMaxL;
+  short2* upd = reinterpret_cast<short2*>(kqs0 + nwarps * kMaxL);
+  int* uptr = reinterpret_cast<int*>(upd + nupd);
+  short* e2s = reinterpret_cast<short*>(uptr + kSlots + 1);
+  for (int e = threadIdx.x; e < nupd; e += blockDim.x) upd[e] = upd_g[e];
+  for (int s = threadIdx.x; s <= kSlots; s += blockDim.x) uptr[s] = uptr_g[s];
+  __syncthreads();
+  for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
+    for (int e = uptr[s]; e < uptr[s + 1]; ++e) e2s[e] = (short)s;
+  __syncthreads();
+
   const BoxDesc bx = boxes[blockIdx.x];
-  const long long P = bx.P;
   T* Fb = F + bx.foff;
+  const long long* qoff = qoff_g + bx.poff;
+  const int* qcp = qcp_g + bx.poff;
   const int* lp = lptr + bx.loff;
+  const int rbase[3] = {kCBase, kGBase, kFBase}, rdiag[3] = {kCDiag, kGDiag, kFDiag}, rend[3] = {kCEnd, kGEnd, kFEnd};
   for (int w = 0; w < bx.nlev; ++w) {
-    for (int q = lp[w] + threadIdx.x; q < lp[w + 1]; q += blockDim.x) {
+    for (int q = lp[w] + warp; q < lp[w + 1]; q += nwarps) {
       const int lex = perm[bx.poff + q];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
       for (int c = 0; c < 3; ++c) {
-        for (int s = c_base[c]; s < c_diag[c]; ++s) {
+        const int base = rbase[c], dg = rdiag[c], end = rend[c];
+        const int e0 = uptr[base], e1 = uptr[dg];
+        // 1. pivots and neighbour positions of the L-slots
+        for (int s = base + lane; s < dg; s += 32) {
           const int ax = kx + c_dx[s], ay = ky + c_dy[s], az = kz + c_dz[s], at = kt + c_dt[s];
-          if (ax < 0 || ax >= bx.lx || ay < 0 || ay >= bx.ly || az < 0 || az >= bx.lz || at < 0 || at >= bx.lt)
-            continue;
-          const int klex = ax + bx.lx * (ay + bx.ly * (az + bx.lz * at));
-          const long long kq = iperm[bx.poff + klex];
-          const T aik = Fb[(size_t)s * P + q];
-          if (aik == (T)0) continue;
-          const T ukk = Fb[(size_t)c_diag[c_comp[s]] * P + kq];
-          const T l = aik / ukk;
-          Fb[(size_t)s * P + q] = l;
-          for (int e = uptr[s]; e < uptr[s + 1]; ++e) {
-            const short2 u = upd[e];
-            Fb[(size_t)u.y * P + q] -= l * Fb[(size_t)u.x * P + kq];
-          }
+          int kq = -1;
+          if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt)
+            kq = iperm[bx.poff + ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))];
+          kqs[s - base] = kq;
+          piv[s - base] = kq >= 0 ? Fb[slot_addr(qoff, qcp, kq, c_diag[c_comp[s]])] : (T)1;
         }
-        const T dg = Fb[(size_t)c_diag[c] * P + q];
-        if (!(fabs((double)dg) > 1e-300) || !isfinite((double)dg)) atomicExch(status, 1);
+        // 2. the row itself
+        for (int i = lane; i < end - base; i += 32) rowb[i] = Fb[slot_addr(qoff, qcp, q, base + i)];
+        __syncwarp();
+        // 3. every u_kj the elimination will read
+        for (int e = e0 + lane; e < e1; e += 32) {
+          const int kq = kqs[e2s[e] - base];
+          gath[e - e0] = kq >= 0 ? Fb[slot_addr(qoff, qcp, kq, upd[e].x)] : (T)0;
+        }
+        __syncwarp();
+        // 4. IKJ elimination in shared memory
+        for (int s = base; s < dg; ++s) {
+          if (kqs[s - base] < 0) continue;          // column outside the box: value 0, nothing to do
+          const T l = rowb[s - base] / piv[s - base];
+          __syncwarp();
+          if (lane == 0) rowb[s - base] = l;
+          for (int e = uptr[s] + lane; e < uptr[s + 1]; e += 32) {
+            const short2 u = upd[e];
+            rowb[u.y - base] -= l * gath[e - e0];
+          }
+          __syncwarp();
+        }
+        // 5. write back and check the pivot
+        for (int i = lane; i < end - base; i += 32) Fb[slot_addr(qoff, qcp, q, base + i)] = rowb[i];
+        if (lane == 0) {
+          const double d = (double)rowb[dg - base];
+          if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
   }
 }
 
-// z = sum_boxes (R^0)^T M^{-1} R^delta r; one CTA per box.
-template <typename T>
-__global__ void __launch_bounds__(256) ras_solve(const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
-                                                 const int* __restrict__ lptr, const T* __restrict__ F,
-                                                 T* __restrict__ V, const double* __restrict__ r,
-                                                 double* __restrict__ z, int nx, int ny, int N) {
-  __shared__ int off[kSlots];
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait: gives up after `limit` polls and reports it through *failed.
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, int* failed) {
+  constexpr long long kLimit = 1LL << 26;
+  for (long long it = 0; !mbar_try_wait(bar, parity); ++it)
+    if (it > kLimit) {
+      atomicExch(failed, 2);
+      return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Subdomain solve z = sum_boxes (R^0)^T M^{-1} R^delta r: one CTA per box,
+// kLanes lanes per point, one chunk of points per step.  Each lane takes every
+// kLanes-th row of the chunk's block in shared memory; the loops have
+// compile-time trip counts and a shuffle reduction closes each row.
+// With SMEM the box's padded local vector lives in shared memory as well.
+// ---------------------------------------------------------------------------
+constexpr int kLanes = 4;
+constexpr size_t kSmemLimit = 227 * 1024;
+constexpr int kSolveHeader = 2048;   // off[] table and the two mbarriers
+
+// sum over block rows [R0, R1) of B[r*cp + j] * vp[off[r + SOFF]]
+template <int R0, int R1, int SOFF, typename T>
+__device__ __forceinline__ T row_dot(const T* __restrict__ B, int cp, int j, const int* __restrict__ off,
+                                     const T* vp, int lane, bool act) {
+  T acc = 0;
+#pragma unroll
+  for (int k = 0; k < (R1 - R0 + kLanes - 1) / kLanes; ++k) {
+    const int r = R0 + lane + k * kLanes;
+    if (act && r < R1) acc += B[r * cp + j] * vp[off[r + SOFF]];
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  return acc;
+}
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
+    const BoxDesc* __restrict__ boxes, const int* __restrict__ perm, const Chunk* __restrict__ chunks,
+    const T* __restrict__ F, T* __restrict__ V, const double* __restrict__ r, double* __restrict__ z, int nx, int ny,
+    int N, int* __restrict__ status) {
+  static_assert((ChunkCfg<T>::CH * kLanes) % 32 == 0, "the solve needs full warps");
+  extern __shared__ __align__(128) unsigned char smem[];
+  int* off = reinterpret_cast<int*>(smem);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
+  T* buf0 = reinterpret_cast<T*>(smem + kSolveHeader);
+  T* buf1 = buf0 + (size_t)kLRanks * ChunkCfg<T>::CHP;
   const BoxDesc bx = boxes[blockIdx.x];
   const long long P = bx.P;
   const T* Fb = F + bx.foff;
-  T* v = V + bx.voff;
-  const int* lp = lptr + bx.loff;
   const int px = bx.lx + 2, py = bx.ly + 2, pz = bx.lz + 2;
   const long long sy = px, sz = (long long)px * py, st = (long long)px * py * pz;
+  const long long npad = 3 * st * (bx.lt + 2);
+  T* v = SMEM ? buf1 + (size_t)kLRanks * ChunkCfg<T>::CHP : V + bx.voff;
+  const int nch = bx.cend - bx.cbeg;
+  const Chunk* ck = chunks + bx.cbeg;
   for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
     off[s] = (int)(3 * (c_dx[s] + sy * c_dy[s] + sz * c_dz[s] + st * c_dt[s]) + c_comp[s]);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  if (SMEM)
+    for (long long i = threadIdx.x; i < npad; i += blockDim.x) v[i] = (T)0;
+  __syncthreads();
+  // stream the L block of chunk 0 while the right-hand side is gathered
+  unsigned phase = 0;   // bit b = parity of the next completion of bar[b]
+  auto issue = [&](int i, bool upper, int b) {
+    const Chunk c = ck[i];
+    const unsigned rows = upper ? kURanks : kLRanks;
+    const unsigned bytes = rows * (unsigned)c.cp * (unsigned)sizeof(T);
+    const T* src = Fb + c.off + (upper ? (long long)kLRanks * c.cp : 0);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[b], bytes);
+    bulk_g2s(b ? buf1 : buf0, src, bytes, &bar[b]);
+  };
+  if (threadIdx.x == 0 && nch > 0) issue(0, false, 0);
   // gather R^delta r into the padded local vector
   for (long long q = threadIdx.x; q < P; q += blockDim.x) {
     const int kx = (int)(q % bx.lx), ky = (int)((q / bx.lx) % bx.ly), kz = (int)((q / (bx.lx * bx.ly)) % bx.lz);
     const int kt = (int)(q / ((long long)bx.lx * bx.ly * bx.lz));
-    const long long g = ((long long)(bx.t0 + kt) * N + (bx.x0 + kx) + (long long)nx * ((bx.y0 + ky) + (long long)ny * (bx.z0 + kz))) * 3;
+    const long long g =
+        ((long long)(bx.t0 + kt) * N + (bx.x0 + kx) + (long long)nx * ((bx.y0 + ky) + (long long)ny * (bx.z0 + kz))) * 3;
     const long long pq = 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
     v[pq] = (T)r[g];
     v[pq + 1] = (T)r[g + 1];
     v[pq + 2] = (T)r[g + 2];
   }
   __syncthreads();
-  // forward sweep with the unit lower factor
-  for (int w = 0; w < bx.nlev; ++w) {
-    for (int q = lp[w] + threadIdx.x; q < lp[w + 1]; q += blockDim.x) {
-      const int lex = perm[bx.poff + q];
+  const int lane = threadIdx.x & (kLanes - 1), j = threadIdx.x / kLanes;
+  // forward sweep with the unit lower factor; rows C, G, f of a point in turn
+  for (int i = 0; i < nch; ++i) {
+    const int b = i & 1;
+    if (threadIdx.x == 0) {
+      if (i + 1 < nch) issue(i + 1, false, b ^ 1);
+      else issue(nch - 1, true, b ^ 1);          // first U block of the backward sweep
+    }
+    mbar_wait(&bar[b], (phase >> b) & 1u, status);
+    phase ^= 1u << b;
+    const Chunk c = ck[i];
+    const T* B = b ? buf1 : buf0;
+    const bool act = j < c.n;
+    T* vp = v;
+    T v0 = 0, v1 = 0, v2 = 0;
+    if (act) {
+      const int lex = perm[bx.poff + c.q0 + j];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      T* vp = v + 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
-      for (int c = 0; c < 3; ++c) {
-        T acc = vp[c];
-        for (int s = c_base[c]; s < c_diag[c]; ++s) acc -= Fb[(size_t)s * P + q] * vp[off[s]];
-        vp[c] = acc;
-      }
+      vp = v + 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
+      v0 = vp[0];
+      v1 = vp[1];
+      v2 = vp[2];
     }
+    T acc = row_dot<0, 80, 0>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) vp[0] = v0 - acc;
+    __syncwarp();
+    acc = row_dot<80, 94, 28>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) vp[1] = v1 - acc;
+    __syncwarp();
+    acc = row_dot<94, 175, 70>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) vp[2] = v2 - acc;
     __syncthreads();
   }
-  // backward sweep with the upper factor
-  for (int w = bx.nlev - 1; w >= 0; --w) {
-    for (int q = lp[w] + threadIdx.x; q < lp[w + 1]; q += blockDim.x) {
-      const int lex = perm[bx.poff + q];
+  // backward sweep with the upper factor; rows f, G, C of a point in turn
+  for (int k = 0; k < nch; ++k) {
+    const int i = nch - 1 - k;
+    const int b = (nch + k) & 1;
+    if (threadIdx.x == 0 && k + 1 < nch) issue(i - 1, true, b ^ 1);
+    mbar_wait(&bar[b], (phase >> b) & 1u, status);
+    phase ^= 1u << b;
+    const Chunk c = ck[i];
+    const T* B = b ? buf1 : buf0;
+    const bool act = j < c.n;
+    T* vp = v;
+    T v0 = 0, v1 = 0, v2 = 0, d0 = 1, d1 = 1, d2 = 1;
+    if (act) {
+      const int lex = perm[bx.poff + c.q0 + j];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      T* vp = v + 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
-      for (int c = 2; c >= 0; --c) {
-        T acc = vp[c];
-        const int end = c_base[c] + c_count[c];
-        for (int s = c_diag[c] + 1; s < end; ++s) acc -= Fb[(size_t)s * P + q] * vp[off[s]];
-        vp[c] = acc / Fb[(size_t)c_diag[c] * P + q];
-      }
+      vp = v + 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
+      v0 = vp[0];
+      v1 = vp[1];
+      v2 = vp[2];
+      d0 = B[0 * c.cp + j];
+      d1 = B[28 * c.cp + j];
+      d2 = B[70 * c.cp + j];
     }
+    T acc = row_dot<71, 151, 175>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) vp[2] = (v2 - acc) / d2;
+    __syncwarp();
+    acc = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) vp[1] = (v1 - acc) / d1;
+    __syncwarp();
+    acc = row_dot<1, 28, 80>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) vp[0] = (v0 - acc) / d0;
     __syncthreads();
   }
   // scatter the owned part: (R^0)^T
@@ -300,6 +548,12 @@ std::vector<std::pair<int, int>> parts(int n, int p) {
   return out;
 }
 
+template <typename T>
+size_t solve_smem(long long max_pad, bool smem_vec) {
+  const size_t bufs = 2 * (size_t)kLRanks * ChunkCfg<T>::CHP * sizeof(T);
+  return kSolveHeader + bufs + (smem_vec ? (size_t)max_pad * sizeof(T) : 0);
+}
+
 }  // namespace
 
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
@@ -320,8 +574,15 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     return KKT_ERR_ARG;
   }
   const SlotTables& T = tables();
+  if (T.base[0] != kCBase || T.diag[0] != kCDiag || T.base[1] != kGBase || T.diag[1] != kGDiag ||
+      T.base[2] != kFBase || T.diag[2] != kFDiag || T.base[2] + T.count[2] != kFEnd) {
+    set_error("ras_setup: internal slot table mismatch");
+    return KKT_ERR_ARG;
+  }
   static bool consts_done = false;   // constant memory is per module; upload once per process
   if (!consts_done) {
+    short rank[kSlots];
+    for (int s = 0; s < kSlots; ++s) rank[s] = (short)slot_rank(s);
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dt, T.dt, kSlots));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dz, T.dz, kSlots));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dy, T.dy, kSlots));
@@ -330,6 +591,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_base, T.base, sizeof(T.base)));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_count, T.count, sizeof(T.count)));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_diag, T.diag, sizeof(T.diag)));
+    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_rank, rank, sizeof(rank)));
     consts_done = true;
   }
 
@@ -337,10 +599,14 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (!m) return KKT_ERR_NOMEM;
   m->prob = p;
   m->prec = factor_prec;
+  const int CH = factor_prec == 64 ? ChunkCfg<double>::CH : ChunkCfg<float>::CH;
+  auto stride = [&](int n) { return factor_prec == 64 ? chunk_stride<double>(n) : chunk_stride<float>(n); };
   std::vector<std::pair<int, int>> pr[4];
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   std::vector<BoxDesc> boxes;
-  std::vector<int> perm, iperm, lptr;
+  std::vector<int> perm, iperm, lptr, qcp;
+  std::vector<long long> qoff;
+  std::vector<Chunk> chunks;
   long long foff = 0, voff = 0;
   for (int it = 0; it < nsub[3]; ++it)
     for (int iz = 0; iz < nsub[2]; ++iz)
@@ -363,7 +629,6 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           b.voff = voff;
           b.poff = (long long)perm.size();
           b.loff = (long long)lptr.size();
-          foff += b.P * kSlots;
           voff += 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2);
           // counting sort of the points by wavefront
           std::vector<int> cnt(b.nlev + 1, 0);
@@ -386,11 +651,33 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
                 }
           perm.insert(perm.end(), bp.begin(), bp.end());
           iperm.insert(iperm.end(), bi.begin(), bi.end());
+          // chunks of each wavefront and the storage offset of every point
+          b.cbeg = (int)chunks.size();
+          long long off = 0;
+          for (int w = 0; w < b.nlev; ++w)
+            for (int q0 = cnt[w]; q0 < cnt[w + 1]; q0 += CH) {
+              Chunk c{};
+              c.q0 = q0;
+              c.n = std::min(CH, cnt[w + 1] - q0);
+              c.cp = stride(c.n);
+              c.off = off;
+              for (int jj = 0; jj < c.n; ++jj) {
+                qoff.push_back(off + jj);
+                qcp.push_back(c.cp);
+              }
+              off += (long long)kSlots * c.cp;
+              chunks.push_back(c);
+            }
+          b.cend = (int)chunks.size();
+          foff += off;
           boxes.push_back(b);
         }
   m->nbox = (int)boxes.size();
   m->boxes_h = boxes;
   m->fcount = foff;
+  m->max_pad = 0;
+  for (const BoxDesc& b : boxes)
+    m->max_pad = std::max(m->max_pad, 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2));
   const size_t esz = factor_prec == 64 ? sizeof(double) : sizeof(float);
   auto fail = [&](kkt_status st, const char* what) {
     cudaGetLastError();
@@ -402,6 +689,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->perm, perm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->iperm, iperm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->lptr, lptr.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&m->qoff, qoff.size() * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&m->qcp, qcp.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
       cudaMalloc(&m->uptr, T.uptr.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->upd, T.upd.size() * sizeof(short2)) != cudaSuccess ||
       cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * esz) != cudaSuccess ||
@@ -412,12 +702,16 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (e == cudaSuccess) e = cudaMemcpy(m->perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->lptr, lptr.data(), lptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->qoff, qoff.data(), qoff.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->qcp, qcp.data(), qcp.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->uptr, T.uptr.data(), T.uptr.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->upd, T.upd.data(), T.upd.size() * sizeof(short2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
   if (e != cudaSuccess) return fail(KKT_ERR_CUDA, cudaGetErrorString(e));
-  kkt_status st = ras_factor(m);
+  kkt_status st = ras_factor(m, nullptr);
   if (st != KKT_OK) {
     ras_destroy(m);
     return st;
@@ -426,22 +720,59 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   return KKT_OK;
 }
 
-kkt_status ras_factor(ras_precond* m) {
+namespace {
+
+template <typename T>
+kkt_status launch_factor(ras_precond* m, cudaStream_t s) {
+  const int warps = sizeof(T) == 8 ? 8 : 16;
+  const int nupd = (int)tables().upd.size();
+  const size_t smem = FactorSmem<T>::bytes(warps, nupd);
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ilu0_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ilu0_factor<T><<<m->nbox, 32 * warps, smem, s>>>(m->boxes, m->perm, m->iperm, m->lptr, m->qoff, m->qcp, m->uptr,
+                                                   m->upd, nupd, (T*)m->F, m->status);
+  KKT_COUNT(1);
+  KKT_TRY_CUDA(cudaGetLastError());
+  return KKT_OK;
+}
+
+template <typename T>
+kkt_status launch_solve(ras_precond* m, const double* r, double* z, cudaStream_t s) {
+  const kkt_problem* p = m->prob;
+  const int threads = ChunkCfg<T>::CH * kLanes;
+  const size_t with_vec = solve_smem<T>(m->max_pad, true);
+  if (with_vec <= kSmemLimit) {
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)with_vec));
+    ras_solve<T, true><<<m->nbox, threads, with_vec, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, (T*)m->V, r,
+                                                          z, p->nx, p->ny, p->N, m->status);
+  } else {
+    const size_t smem = solve_smem<T>(m->max_pad, false);
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ras_solve<T, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, (T*)m->V, r, z,
+                                                       p->nx, p->ny, p->N, m->status);
+  }
+  KKT_COUNT(1);
+  KKT_TRY_CUDA(cudaGetLastError());
+  return KKT_OK;
+}
+
+}  // namespace
+
+kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   const DevProblem dp = m->prob->dev();
   dim3 g(152, m->nbox);
+  KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
   if (m->prec == 64) {
-    gather_matrix<double><<<g, 256>>>(dp, m->boxes, m->perm, (double*)m->F);
-    ilu0_factor<double><<<m->nbox, 256>>>(m->boxes, m->perm, m->iperm, m->lptr, m->uptr, m->upd, (double*)m->F,
-                                          m->status);
+    gather_matrix<double><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->qoff, m->qcp, (double*)m->F);
+    KKT_COUNT(1);
+    KKT_TRY(launch_factor<double>(m, s));
   } else {
-    gather_matrix<float><<<g, 256>>>(dp, m->boxes, m->perm, (float*)m->F);
-    ilu0_factor<float><<<m->nbox, 256>>>(m->boxes, m->perm, m->iperm, m->lptr, m->uptr, m->upd, (float*)m->F,
-                                         m->status);
+    gather_matrix<float><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->qoff, m->qcp, (float*)m->F);
+    KKT_COUNT(1);
+    KKT_TRY(launch_factor<float>(m, s));
   }
-  KKT_TRY_CUDA(cudaGetLastError());
-  KKT_TRY_CUDA(cudaDeviceSynchronize());
   int st = 0;
-  KKT_TRY_CUDA(cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost));
+  KKT_TRY_CUDA(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KKT_TRY_CUDA(cudaStreamSynchronize(s));
   if (st != 0) {
     set_error("ras_setup: zero or non-finite pivot in a subdomain ILU(0)");
     return KKT_ERR_ZERO_PIVOT;
@@ -450,14 +781,18 @@ kkt_status ras_factor(ras_precond* m) {
 }
 
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s) {
-  const kkt_problem* p = m->prob;
-  if (m->prec == 64)
-    ras_solve<double><<<m->nbox, 256, 0, s>>>(m->boxes, m->perm, m->lptr, (const double*)m->F, (double*)m->V, r, z,
-                                              p->nx, p->ny, p->N);
-  else
-    ras_solve<float><<<m->nbox, 256, 0, s>>>(m->boxes, m->perm, m->lptr, (const float*)m->F, (float*)m->V, r, z,
-                                             p->nx, p->ny, p->N);
-  KKT_TRY_CUDA(cudaGetLastError());
+  TimedScope timed(&m->timing, s);
+  if (m->prec == 64) return launch_solve<double>(m, r, z, s);
+  return launch_solve<float>(m, r, z, s);
+}
+
+kkt_status ras_check(ras_precond* m) {
+  int st = 0;
+  KKT_TRY_CUDA(cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st == 2) {
+    set_error("ras_apply: a subdomain solve gave up waiting for its factor copy");
+    return KKT_ERR_CUDA;
+  }
   return KKT_OK;
 }
 
@@ -478,6 +813,46 @@ extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void
   return ras_launch(m, r, z, (cudaStream_t)stream);
 }
 
+extern "C" kkt_status ras_info(const ras_precond* m, int* nbox, long long* points, long long* factor_values,
+                               int* value_bytes) {
+  if (!m) {
+    set_error("ras_info: null argument");
+    return KKT_ERR_ARG;
+  }
+  long long pts = 0;
+  for (const BoxDesc& b : m->boxes_h) pts += b.P;
+  if (nbox) *nbox = m->nbox;
+  if (points) *points = pts;
+  if (factor_values) *factor_values = m->fcount;
+  if (value_bytes) *value_bytes = m->prec == 64 ? 8 : 4;
+  return KKT_OK;
+}
+
+extern "C" kkt_status ras_refactor(ras_precond* m, void* stream) {
+  if (!m) {
+    set_error("ras_refactor: null argument");
+    return KKT_ERR_ARG;
+  }
+  return ras_factor(m, (cudaStream_t)stream);
+}
+
+extern "C" kkt_status ras_timing_read(ras_precond* m, double* total_ms, long long* launches) {
+  if (!m) {
+    set_error("ras_timing_read: null argument");
+    return KKT_ERR_ARG;
+  }
+  m->timing.drain();
+  if (total_ms) *total_ms = m->timing.total_ms;
+  if (launches) *launches = m->timing.count;
+  return KKT_OK;
+}
+
+extern "C" kkt_status kkt_timing_reset(kkt_problem* p, ras_precond* m) {
+  if (p) p->mv_timing.reset();
+  if (m) m->timing.reset();
+  return KKT_OK;
+}
+
 extern "C" void ras_destroy(ras_precond* m) {
   if (!m) return;
   cudaFree(m->boxes);
@@ -486,6 +861,9 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->lptr);
   cudaFree(m->uptr);
   cudaFree(m->upd);
+  cudaFree(m->qoff);
+  cudaFree(m->qcp);
+  cudaFree(m->chunks);
   cudaFree(m->F);
   cudaFree(m->V);
   cudaFree(m->status);

@@ -6,6 +6,16 @@
 // slots per point: C row 2*27*2 = 108, G row 2*(27+1) = 56, f row 3*27*2 = 162
 constexpr int kSlots = 326;
 
+// A run of at most CH points of one wavefront whose factor values form one
+// contiguous block [slot rank][cp] (cp >= n, chosen per precision).
+struct Chunk {
+  int q0;                      // first point (wavefront order, box-local)
+  int n;                       // points
+  int cp;                      // row stride of the block
+  int pad_;
+  long long off;               // element offset of the block within the box
+};
+
 // One subdomain box (extended set, owned set, storage offsets).
 struct BoxDesc {
   int x0, y0, z0, t0;          // origin of the extended box (global node / level)
@@ -17,6 +27,7 @@ struct BoxDesc {
   long long voff;              // offset of the box's padded local vector (elements)
   long long poff;              // offset into perm / iperm
   long long loff;              // offset into the wavefront pointers
+  int cbeg, cend;              // chunk range
 };
 
 struct ras_precond {
@@ -24,6 +35,7 @@ struct ras_precond {
   int prec = 64;               // factor / solve precision (64 or 32)
   int nbox = 0;
   long long fcount = 0;        // factor values
+  long long max_pad = 0;       // largest padded local vector (elements)
   std::vector<BoxDesc> boxes_h;
   BoxDesc* boxes = nullptr;
   int* perm = nullptr;         // wavefront order -> lexicographic local index
@@ -31,12 +43,17 @@ struct ras_precond {
   int* lptr = nullptr;         // wavefront pointers per box (nlev + 1 each)
   int* uptr = nullptr;         // factorisation update lists
   short2* upd = nullptr;
+  long long* qoff = nullptr;   // per point: offset of its column in its chunk block
+  int* qcp = nullptr;          // per point: row stride of its chunk block
+  Chunk* chunks = nullptr;
   void* F = nullptr;           // factor values
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;
+  TimingLog timing;            // subdomain-solve launches
 };
 
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
                       ras_precond** out);
-kkt_status ras_factor(ras_precond* m);
+kkt_status ras_factor(ras_precond* m, cudaStream_t s);
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s);
+kkt_status ras_check(ras_precond* m);

@@ -123,7 +123,10 @@ Grid4 grid_of(const kkt_problem* p) { return Grid4{p->nx, p->ny, p->nz, p->L, p-
 struct KktOp : Operator {
   kkt_problem* p;
   explicit KktOp(kkt_problem* p_) : p(p_) {}
-  kkt_status apply(const double* x, double* y, cudaStream_t s) override { return launch_matvec64(p->dev(), x, y, s); }
+  kkt_status apply(const double* x, double* y, cudaStream_t s) override {
+    TimedScope t(&p->mv_timing, s);
+    return launch_matvec64(p->dev(), x, y, s);
+  }
 };
 
 struct RasOp : Operator {
@@ -137,6 +140,7 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   kkt_problem* pc = c->cp;
   const Grid4 gf = grid_of(pf), gc = grid_of(pc);
   restrict_kernel<<<(unsigned)((pc->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   KktOp Ac(pc);
   RasOp Mc(c->cras);
@@ -145,6 +149,7 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   if (r.status < 0) return r.status;
   c->last_coarse_iters = r.iters;
   interp_kernel<<<(unsigned)((pf->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
+  KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   KKT_TRY(launch_residual(pf->dev(), x, c->y, c->t, s));   // t = x - F_h y
   KKT_TRY(ras_launch(fine, c->t, z, s));
@@ -240,6 +245,14 @@ extern "C" kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const 
   return two_level(c, fine, x, z, (cudaStream_t)stream);
 }
 
+extern "C" kkt_status coarse_refactor(coarse_level* c, void* stream) {
+  if (!c) {
+    set_error("coarse_refactor: null argument");
+    return KKT_ERR_ARG;
+  }
+  return ras_factor(c->cras, (cudaStream_t)stream);
+}
+
 extern "C" void coarse_destroy(coarse_level* c) {
   if (!c) return;
   ras_destroy(c->cras);
@@ -280,6 +293,8 @@ extern "C" kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* 
   Operator* M = c ? (Operator*)&T : (m ? (Operator*)&R : nullptr);
   GmresResult res;
   KKT_TRY(gmres_run(A, M, b, x, ws, restart, rtol, maxit, true, false, &res, s));
+  if (m) KKT_TRY(ras_check(m));
+  if (c) KKT_TRY(ras_check(c->cras));
   if (iters) *iters = res.iters;
   if (true_relres) *true_relres = res.relres;
   return res.status;

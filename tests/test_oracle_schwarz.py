@@ -179,3 +179,24 @@ def test_flexible_and_standard_gmres_agree_for_a_fixed_preconditioner():
     # an exact preconditioner gives one step
     r3 = krylov.gmres(lambda u: A @ u, b, lambda v: np.linalg.solve(A, v), restart=8, rtol=1e-10)
     assert r3.iterations == 1
+
+
+def test_box_assembly_is_the_principal_submatrix():
+    p, F = _small(cells=(4, 3, 3), M=5)
+    for b in schwarz.boxes(p, (2, 2, 1, 2), 1)[::3]:
+        idx, _ = schwarz.box_unknowns(p, b)
+        nodes, levels = schwarz.box_nodes_levels(p, b)
+        Fb = kkt.assemble_box(p, nodes, levels)
+        assert abs(Fb - F[idx][:, idx]).max() == 0.0
+
+
+def test_partial_ilu0_is_the_leading_block_of_the_full_one():
+    p, F = _small()
+    b = schwarz.boxes(p, (2, 1, 1, 2), 1)[1]
+    idx, _ = schwarz.box_unknowns(p, b)
+    Aloc = F[idx][:, idx].tocsr()
+    full = schwarz.ILU0(Aloc, schwarz.local_pattern(p, idx))
+    part = schwarz.ILU0(Aloc, schwarz.local_pattern(p, idx, rows=40), rows=40)
+    for i in range(40):
+        assert part.L[i] == full.L[i] and part.diag[i] == full.diag[i]
+        assert part.U[i] == {j: v for j, v in full.U[i].items() if j < 40}
