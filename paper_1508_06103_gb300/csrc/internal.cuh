@@ -109,6 +109,8 @@ kkt_status launch_matvec32(const DevProblem& p, const float* x, float* y, cudaSt
 kkt_status launch_residual(const DevProblem& p, const double* b, const double* x, double* r, cudaStream_t s);
 kkt_status launch_residual32(const DevProblem& p, const double* b, const double* x, double* r,
                              float* x32, float* y32, cudaStream_t s);
+kkt_status launch_matvec32_d(const DevProblem& p, const double* x, double* y, float* x32, float* y32,
+                             cudaStream_t s);
 
 // problem.cu
 kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_cell, const double* v_cell,

@@ -69,6 +69,20 @@ struct SlotTables {
   // entries [uptr[s], uptr[s+1]) of (t, s2): a[s2] -= l * u_k[t]
   std::vector<int> uptr;
   std::vector<short2> upd;
+  // Level schedule of the elimination of one row.  An L-slot's multiplier is
+  // final once every slot that updates it has been processed, so the L-slots
+  // of a row type split into dependency levels (16 / 7 / 16 for C / G / f
+  // instead of 80 / 14 / 81 sequential steps).  Per row type and level:
+  // the slots whose multiplier is formed (lslots) and the update targets, each
+  // with the range of its contributions (s, e): a[s2] -= sum l_s * u_e.
+  std::vector<int> lev_ptr[3];        // level -> range in lslots / tgts (two entries per level)
+  std::vector<short> lslots;
+  std::vector<int> tptr_lev;          // per level of every row type: range of targets
+  std::vector<short4> tgts;           // (s2, contribution begin, end, 0)
+  std::vector<short2> cons;           // (slot s, update index e)
+  int nlev[3];
+  int lev_base[3];                    // first level index of each row type in tptr_lev / lptr_lev
+  std::vector<int> lptr_lev;          // per level: range in lslots
 };
 
 SlotTables build_tables() {
@@ -113,6 +127,41 @@ SlotTables build_tables() {
     }
   for (int q = 0; q < kSlots; ++q) T.uptr[q + 1] = T.uptr[q] + (int)lists[q].size();
   for (int q = 0; q < kSlots; ++q) T.upd.insert(T.upd.end(), lists[q].begin(), lists[q].end());
+  // dependency levels of the L-slots and the pull-form update lists per level
+  int glev = 0;
+  T.lptr_lev.push_back(0);
+  T.tptr_lev.push_back(0);
+  for (int c = 0; c < 3; ++c) {
+    std::vector<int> lev(kSlots, 0);
+    int depth = 0;
+    for (int q = T.base[c]; q < T.diag[c]; ++q) {
+      int d = 0;
+      for (int p2 = T.base[c]; p2 < q; ++p2)
+        for (int e = T.uptr[p2]; e < T.uptr[p2 + 1]; ++e)
+          if (T.upd[e].y == q) d = std::max(d, lev[p2] + 1);
+      lev[q] = d;
+      depth = std::max(depth, d + 1);
+    }
+    T.nlev[c] = depth;
+    T.lev_base[c] = glev;
+    for (int l = 0; l < depth; ++l, ++glev) {
+      for (int q = T.base[c]; q < T.diag[c]; ++q)
+        if (lev[q] == l) T.lslots.push_back((short)q);
+      T.lptr_lev.push_back((int)T.lslots.size());
+      // targets of the updates issued by this level's slots
+      std::vector<std::vector<short2>> by_target(kSlots);
+      for (int q = T.base[c]; q < T.diag[c]; ++q)
+        if (lev[q] == l)
+          for (int e = T.uptr[q]; e < T.uptr[q + 1]; ++e) by_target[T.upd[e].y].push_back(make_short2((short)q, (short)e));
+      for (int s2 = 0; s2 < kSlots; ++s2)
+        if (!by_target[s2].empty()) {
+          const short b0 = (short)T.cons.size();
+          T.cons.insert(T.cons.end(), by_target[s2].begin(), by_target[s2].end());
+          T.tgts.push_back(make_short4((short)s2, b0, (short)T.cons.size(), 0));
+        }
+      T.tptr_lev.push_back((int)T.tgts.size());
+    }
+  }
   return T;
 }
 
@@ -123,7 +172,8 @@ const SlotTables& tables() {
 
 __constant__ int8_t c_dt[kSlots], c_dz[kSlots], c_dy[kSlots], c_dx[kSlots], c_comp[kSlots];
 __constant__ int c_base[3], c_count[3], c_diag[3];
-__constant__ short c_rank[kSlots];   // slot -> row of the chunk block
+__constant__ short c_rank[kSlots];          // slot -> row of the chunk block
+__constant__ short c_slot_of_rank[kSlots];  // row of the chunk block -> slot
 
 // Slot ranges of the three row types (checked against the tables on the host).
 constexpr int kCBase = 0, kCDiag = 80, kCEnd = 108;
@@ -170,113 +220,154 @@ int chunk_stride(int n) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// Matrix entry of F_h in row (point, type c) at slot s; j node, n level.
-__device__ double kkt_entry(const DevProblem& p, int c, int s, int j, int n, int d) {
-  const double tau = p.tau, th = p.theta, th1 = 1.0 - p.theta;
-  const int dt = c_dt[s], cc = c_comp[s];
-  const size_t ci = (size_t)d * p.N + j;
-  const bool dirj = p.dir[j] != 0;
-  if (c == 0) {
-    if (n == 0 || dirj) return (s == c_diag[0]) ? 1.0 : 0.0;
-    if (cc == 0) return dt == 0 ? p.B[ci] + th * tau * p.S[ci] : -p.B[ci] + th1 * tau * p.S[ci];
-    return dt == 0 ? -th * tau * p.B[ci] : -th1 * tau * p.B[ci];
-  }
-  if (c == 1) {
-    if (n == p.M || dirj) return (s == c_diag[1]) ? 1.0 : 0.0;
-    if (cc == 1) return dt == 0 ? p.B[ci] + th * tau * p.ST[ci] : -p.B[ci] + th1 * tau * p.ST[ci];
-    return (dt == 0 ? th1 : th) * tau * p.sens[j];
-  }
-  // f row: time mass / stiffness weights of the linear hats
-  double mt, lt;
-  if (dt == 0) {
-    mt = (n > 0 ? tau / 3 : 0.0) + (n < p.M ? tau / 3 : 0.0);
-    lt = (n > 0 ? 1.0 / tau : 0.0) + (n < p.M ? 1.0 / tau : 0.0);
-  } else {
-    mt = tau / 6;
-    lt = -1.0 / tau;
-  }
-  if (cc == 1) return -mt * p.B[ci];
-  return p.beta1 * lt * p.B[ci] + p.beta2 * mt * p.K[ci];
-}
+// The factorisation works on a point-major copy of the values (all 326 slots of
+// a point contiguous, points in wavefront order), which keeps the U rows a
+// row is eliminated with in a few cache lines; a transpose then writes the
+// chunk blocks the solve streams.
 
-// address of slot s of point q (wavefront order) inside the box's storage
-__device__ __forceinline__ long long slot_addr(const long long* __restrict__ qoff, const int* __restrict__ qcp,
-                                               int q, int s) {
-  return qoff[q] + (long long)c_rank[s] * qcp[q];
-}
-
-// Fill the slot values of every point of every box from the stencil coefficients.
+// Fill the slot values of every point of every box from the stencil
+// coefficients: one warp per point, lanes over the slots (slot tables staged
+// in shared memory, as the lanes index them divergently).
 template <typename T>
-__global__ void gather_matrix(DevProblem p, const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
-                              const long long* __restrict__ qoff_g, const int* __restrict__ qcp_g,
-                              T* __restrict__ F) {
+__global__ void __launch_bounds__(256) gather_matrix(DevProblem p, const BoxDesc* __restrict__ boxes,
+                                                     const int* __restrict__ perm, T* __restrict__ Fpm) {
+  __shared__ int8_t sdt[kSlots], sdz[kSlots], sdy[kSlots], sdx[kSlots], scomp[kSlots];
+  for (int s = threadIdx.x; s < kSlots; s += blockDim.x) {
+    sdt[s] = c_dt[s];
+    sdz[s] = c_dz[s];
+    sdy[s] = c_dy[s];
+    sdx[s] = c_dx[s];
+    scomp[s] = c_comp[s];
+  }
+  __syncthreads();
   const BoxDesc bx = boxes[blockIdx.y];
-  const long long P = bx.P;
-  T* Fb = F + bx.foff;
-  const long long* qoff = qoff_g + bx.poff;
-  const int* qcp = qcp_g + bx.poff;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < P * kSlots;
-       r += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(r / kSlots);
-    const int s = (int)(r - (long long)q * kSlots);
+  T* Fb = Fpm + bx.pmoff;
+  const int lane = threadIdx.x & 31;
+  const double tau = p.tau, th = p.theta, th1 = 1.0 - p.theta;
+  for (long long q = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); q < bx.P;
+       q += (long long)gridDim.x * (blockDim.x >> 5)) {
     const int lex = perm[bx.poff + q];
     const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
     const int kt = lex / (bx.lx * bx.ly * bx.lz);
-    const int c = s < c_base[1] ? 0 : (s < c_base[2] ? 1 : 2);
-    const int nx_ = kx + c_dx[s], ny_ = ky + c_dy[s], nz_ = kz + c_dz[s], nt_ = kt + c_dt[s];
-    double v = 0.0;
-    if (nx_ >= 0 && nx_ < bx.lx && ny_ >= 0 && ny_ < bx.ly && nz_ >= 0 && nz_ < bx.lz && nt_ >= 0 && nt_ < bx.lt) {
-      const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, gt = bx.t0 + kt;
-      const int j = gx + p.nx * (gy + p.ny * gz);
-      const int d = (c_dx[s] + 1) + 3 * (c_dy[s] + 1) + 9 * (c_dz[s] + 1);
-      v = kkt_entry(p, c, s, j, gt, d);
+    const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, n = bx.t0 + kt;
+    const int j = gx + p.nx * (gy + p.ny * gz);
+    const bool dirj = p.dir[j] != 0;
+    for (int s = lane; s < kSlots; s += 32) {
+      const int c = s < kGBase ? 0 : (s < kFBase ? 1 : 2);
+      const int dt = sdt[s], cc = scomp[s];
+      const int ax = kx + sdx[s], ay = ky + sdy[s], az = kz + sdz[s], at = kt + dt;
+      double v = 0.0;
+      if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
+        const int d = (sdx[s] + 1) + 3 * (sdy[s] + 1) + 9 * (sdz[s] + 1);
+        const size_t ci = (size_t)d * p.N + j;
+        if (c == 0) {
+          if (n == 0 || dirj) v = (s == kCDiag) ? 1.0 : 0.0;
+          else if (cc == 0) v = dt == 0 ? p.B[ci] + th * tau * p.S[ci] : -p.B[ci] + th1 * tau * p.S[ci];
+          else v = dt == 0 ? -th * tau * p.B[ci] : -th1 * tau * p.B[ci];
+        } else if (c == 1) {
+          if (n == p.M || dirj) v = (s == kGDiag) ? 1.0 : 0.0;
+          else if (cc == 1) v = dt == 0 ? p.B[ci] + th * tau * p.ST[ci] : -p.B[ci] + th1 * tau * p.ST[ci];
+          else v = (dt == 0 ? th1 : th) * tau * p.sens[j];
+        } else {
+          // f row: time mass / stiffness weights of the linear hats
+          double mt, lt;
+          if (dt == 0) {
+            mt = (n > 0 ? tau / 3 : 0.0) + (n < p.M ? tau / 3 : 0.0);
+            lt = (n > 0 ? 1.0 / tau : 0.0) + (n < p.M ? 1.0 / tau : 0.0);
+          } else {
+            mt = tau / 6;
+            lt = -1.0 / tau;
+          }
+          v = cc == 1 ? -mt * p.B[ci] : p.beta1 * lt * p.B[ci] + p.beta2 * mt * p.K[ci];
+        }
+      }
+      Fb[q * kSlots + s] = (T)v;
     }
-    Fb[slot_addr(qoff, qcp, q, s)] = (T)v;
+  }
+}
+
+// Chunk blocks [slot rank][cp] of the solve from the point-major factors;
+// one CTA per chunk, staged through shared memory so both sides are contiguous.
+template <typename T>
+__global__ void chunk_transpose(const BoxDesc* __restrict__ boxes, const Chunk* __restrict__ chunks,
+                                const T* __restrict__ Fpm, T* __restrict__ F) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* tile = reinterpret_cast<T*>(smem);
+  const Chunk c = chunks[blockIdx.x];
+  const BoxDesc bx = boxes[c.box];
+  const T* src = Fpm + bx.pmoff + (long long)c.q0 * kSlots;
+  const int nin = c.n * kSlots;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) tile[i] = src[i];
+  __syncthreads();
+  T* dst = F + bx.foff + c.off;
+  const int nout = kSlots * c.cp;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int r = o / c.cp, j = o - r * c.cp;
+    dst[o] = j < c.n ? tile[j * kSlots + c_slot_of_rank[r]] : (T)0;
   }
 }
 
 // ---------------------------------------------------------------------------
 // ILU(0) factorisation: one CTA per box, one warp per point of a wavefront.
-// For each row the warp first gathers, in parallel, every value the IKJ
-// elimination of that row will read (the pivots u_kk and the U entries u_kj of
-// the rows k it eliminates with), then runs the sequential elimination on
-// shared memory with the updates of one pivot spread over the lanes.
+// For each row the warp first gathers into shared memory every value the
+// elimination of that row reads -- the pivots u_kk and the U entries u_kj of
+// the rows k it eliminates with -- with many independent loads in flight per
+// lane (consecutive lanes read consecutive entries of one pivot row), then
+// eliminates in shared memory by dependency level: at each level the row's
+// multipliers l_s = a_s / u_kk are formed, then a[s2] -= sum l_s u_k[t] over
+// the level's updates, one target per lane in a fixed order.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct FactorSmem {
-  static size_t bytes(int warps, int nupd) {
-    return (size_t)nupd * sizeof(short2) + (kSlots + 1) * sizeof(int) + (size_t)nupd * sizeof(short) +
-           (size_t)warps * ((kMaxRow + kMaxUpd + kMaxL) * sizeof(T) + kMaxL * sizeof(int)) + 64;
+struct FactorSchedule {
+  const short2* gtab;         // per update e: (L-slot s, U-slot t of the pivot row)
+  const short4* tgts;
+  const short2* cons;
+  const short* lslots;
+  int ntgts, nlslots, ncons;
+  int nlev[3], lev_base[3], ebase[3], eend[3];
+  int lptr[64], tptr[64];     // per global level: ranges in lslots / tgts (levels of C, G, f)
+};
+
+// Shared-memory layout of the factor kernel: the tables, then one buffer per
+// warp (row values, gathered U entries, reciprocal pivots, neighbour positions).
+struct FactorLayout {
+  size_t gtab, cons, tgts, lsl, warp0, per_warp, total;
+  __host__ __device__ static size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
+  __host__ __device__ FactorLayout(int warps, int ncons, int ntgts, int nlslots, int tsize) {
+    gtab = 0;
+    cons = al(gtab + (size_t)ncons * 4, 8);
+    tgts = al(cons + (size_t)ncons * 4, 8);
+    lsl = tgts + (size_t)ntgts * 8;
+    warp0 = al(lsl + (size_t)nlslots * 2, 16);
+    per_warp = al((size_t)(kMaxRow + kMaxUpd + kMaxL) * tsize + kMaxL * 4, 16);
+    total = warp0 + (size_t)warps * per_warp;
   }
 };
 
 template <typename T>
 __global__ void ilu0_factor(const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
-                            const int* __restrict__ iperm, const int* __restrict__ lptr,
-                            const long long* __restrict__ qoff_g, const int* __restrict__ qcp_g,
-                            const int* __restrict__ uptr_g, const short2* __restrict__ upd_g, int nupd,
-                            T* __restrict__ F, int* __restrict__ status) {
+                            const int* __restrict__ iperm, const int* __restrict__ lptr, const FactorSchedule sched,
+                            T* __restrict__ Fpm, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* rowb = reinterpret_cast<T*>(smem) + (size_t)warp * (kMaxRow + kMaxUpd + kMaxL);
+  const FactorLayout lay(nwarps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T));
+  short2* gtab = reinterpret_cast<short2*>(smem + lay.gtab);
+  short2* cons = reinterpret_cast<short2*>(smem + lay.cons);
+  short4* tgts = reinterpret_cast<short4*>(smem + lay.tgts);
+  short* lsl = reinterpret_cast<short*>(smem + lay.lsl);
+  T* rowb = reinterpret_cast<T*>(smem + lay.warp0 + (size_t)warp * lay.per_warp);
   T* gath = rowb + kMaxRow;
   T* piv = gath + kMaxUpd;
-  int* kqs0 = reinterpret_cast<int*>(reinterpret_cast<T*>(smem) + (size_t)nwarps * (kMaxRow + kMaxUpd + kMaxL));
-  int* kqs = kqs0 + warp * kMaxL;
-  short2* upd = reinterpret_cast<short2*>(kqs0 + nwarps * kMaxL);
-  int* uptr = reinterpret_cast<int*>(upd + nupd);
-  short* e2s = reinterpret_cast<short*>(uptr + kSlots + 1);
-  for (int e = threadIdx.x; e < nupd; e += blockDim.x) upd[e] = upd_g[e];
-  for (int s = threadIdx.x; s <= kSlots; s += blockDim.x) uptr[s] = uptr_g[s];
-  __syncthreads();
-  for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
-    for (int e = uptr[s]; e < uptr[s + 1]; ++e) e2s[e] = (short)s;
+  int* kqs = reinterpret_cast<int*>(piv + kMaxL);
+  for (int i = threadIdx.x; i < sched.ncons; i += blockDim.x) {
+    gtab[i] = sched.gtab[i];
+    cons[i] = sched.cons[i];
+  }
+  for (int i = threadIdx.x; i < sched.ntgts; i += blockDim.x) tgts[i] = sched.tgts[i];
+  for (int i = threadIdx.x; i < sched.nlslots; i += blockDim.x) lsl[i] = sched.lslots[i];
   __syncthreads();
 
   const BoxDesc bx = boxes[blockIdx.x];
-  T* Fb = F + bx.foff;
-  const long long* qoff = qoff_g + bx.poff;
-  const int* qcp = qcp_g + bx.poff;
+  T* Fb = Fpm + bx.pmoff;
   const int* lp = lptr + bx.loff;
   const int rbase[3] = {kCBase, kGBase, kFBase}, rdiag[3] = {kCDiag, kGDiag, kFDiag}, rend[3] = {kCEnd, kGEnd, kFEnd};
   for (int w = 0; w < bx.nlev; ++w) {
@@ -286,39 +377,49 @@ __global__ void ilu0_factor(const BoxDesc* __restrict__ boxes, const int* __rest
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
       for (int c = 0; c < 3; ++c) {
         const int base = rbase[c], dg = rdiag[c], end = rend[c];
-        const int e0 = uptr[base], e1 = uptr[dg];
-        // 1. pivots and neighbour positions of the L-slots
+        const int e0 = sched.ebase[c], e1 = sched.eend[c];
+        // 1. neighbour positions and reciprocal pivots of the L-slots; the row itself
+#pragma unroll 3
         for (int s = base + lane; s < dg; s += 32) {
           const int ax = kx + c_dx[s], ay = ky + c_dy[s], az = kz + c_dz[s], at = kt + c_dt[s];
           int kq = -1;
           if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt)
             kq = iperm[bx.poff + ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))];
           kqs[s - base] = kq;
-          piv[s - base] = kq >= 0 ? Fb[slot_addr(qoff, qcp, kq, c_diag[c_comp[s]])] : (T)1;
+          piv[s - base] = kq >= 0 ? (T)1 / Fb[(long long)kq * kSlots + c_diag[c_comp[s]]] : (T)1;
         }
-        // 2. the row itself
-        for (int i = lane; i < end - base; i += 32) rowb[i] = Fb[slot_addr(qoff, qcp, q, base + i)];
+#pragma unroll 6
+        for (int i = lane; i < end - base; i += 32) rowb[i] = Fb[(long long)q * kSlots + base + i];
         __syncwarp();
-        // 3. every u_kj the elimination will read
+        // 2. every u_kj the elimination reads (0 where the pivot row is outside the box)
+#pragma unroll 8
         for (int e = e0 + lane; e < e1; e += 32) {
-          const int kq = kqs[e2s[e] - base];
-          gath[e - e0] = kq >= 0 ? Fb[slot_addr(qoff, qcp, kq, upd[e].x)] : (T)0;
+          const short2 g = gtab[e];
+          const int kq = kqs[g.x - base];
+          gath[e - e0] = kq >= 0 ? Fb[(long long)kq * kSlots + g.y] : (T)0;
         }
         __syncwarp();
-        // 4. IKJ elimination in shared memory
-        for (int s = base; s < dg; ++s) {
-          if (kqs[s - base] < 0) continue;          // column outside the box: value 0, nothing to do
-          const T l = rowb[s - base] / piv[s - base];
+        // 3. elimination by dependency level, in shared memory (piv holds 1 / u_kk);
+        //    a slot whose column leaves the box has value 0 and gathered entries 0
+        for (int l = sched.lev_base[c]; l < sched.lev_base[c] + sched.nlev[c]; ++l) {
+          for (int i = sched.lptr[l] + lane; i < sched.lptr[l + 1]; i += 32) {
+            const int sl = lsl[i] - base;
+            rowb[sl] *= piv[sl];
+          }
           __syncwarp();
-          if (lane == 0) rowb[s - base] = l;
-          for (int e = uptr[s] + lane; e < uptr[s + 1]; e += 32) {
-            const short2 u = upd[e];
-            rowb[u.y - base] -= l * gath[e - e0];
+          for (int i = sched.tptr[l] + lane; i < sched.tptr[l + 1]; i += 32) {
+            const short4 tg = tgts[i];
+            T acc = 0;
+            for (int k = tg.y; k < tg.z; ++k) {
+              const short2 cn = cons[k];
+              acc += rowb[cn.x - base] * gath[cn.y - e0];
+            }
+            rowb[tg.x - base] -= acc;
           }
           __syncwarp();
         }
-        // 5. write back and check the pivot
-        for (int i = lane; i < end - base; i += 32) Fb[slot_addr(qoff, qcp, q, base + i)] = rowb[i];
+        // 4. write back and check the pivot
+        for (int i = lane; i < end - base; i += 32) Fb[(long long)q * kSlots + base + i] = rowb[i];
         if (lane == 0) {
           const double d = (double)rowb[dg - base];
           if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
@@ -574,6 +675,10 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     return KKT_ERR_ARG;
   }
   const SlotTables& T = tables();
+  if (T.lptr_lev.size() > 64 || T.cons.size() != T.upd.size()) {
+    set_error("ras_setup: internal factorisation schedule too large");
+    return KKT_ERR_ARG;
+  }
   if (T.base[0] != kCBase || T.diag[0] != kCDiag || T.base[1] != kGBase || T.diag[1] != kGDiag ||
       T.base[2] != kFBase || T.diag[2] != kFDiag || T.base[2] + T.count[2] != kFEnd) {
     set_error("ras_setup: internal slot table mismatch");
@@ -581,8 +686,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   }
   static bool consts_done = false;   // constant memory is per module; upload once per process
   if (!consts_done) {
-    short rank[kSlots];
+    short rank[kSlots], inv[kSlots];
     for (int s = 0; s < kSlots; ++s) rank[s] = (short)slot_rank(s);
+    for (int s = 0; s < kSlots; ++s) inv[rank[s]] = (short)s;
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dt, T.dt, kSlots));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dz, T.dz, kSlots));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dy, T.dy, kSlots));
@@ -592,6 +698,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_count, T.count, sizeof(T.count)));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_diag, T.diag, sizeof(T.diag)));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_rank, rank, sizeof(rank)));
+    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_slot_of_rank, inv, sizeof(inv)));
     consts_done = true;
   }
 
@@ -604,10 +711,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   std::vector<std::pair<int, int>> pr[4];
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   std::vector<BoxDesc> boxes;
-  std::vector<int> perm, iperm, lptr, qcp;
-  std::vector<long long> qoff;
+  std::vector<int> perm, iperm, lptr;
   std::vector<Chunk> chunks;
-  long long foff = 0, voff = 0;
+  long long foff = 0, voff = 0, pmoff = 0;
   for (int it = 0; it < nsub[3]; ++it)
     for (int iz = 0; iz < nsub[2]; ++iz)
       for (int iy = 0; iy < nsub[1]; ++iy)
@@ -626,6 +732,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           b.P = (long long)b.lx * b.ly * b.lz * b.lt;
           b.nlev = (b.lx - 1) + 2 * (b.ly - 1) + 4 * (b.lz - 1) + 8 * (b.lt - 1) + 1;
           b.foff = foff;
+          b.pmoff = pmoff;
+          pmoff += b.P * kSlots;
           b.voff = voff;
           b.poff = (long long)perm.size();
           b.loff = (long long)lptr.size();
@@ -657,14 +765,11 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           for (int w = 0; w < b.nlev; ++w)
             for (int q0 = cnt[w]; q0 < cnt[w + 1]; q0 += CH) {
               Chunk c{};
+              c.box = (int)boxes.size();
               c.q0 = q0;
               c.n = std::min(CH, cnt[w + 1] - q0);
               c.cp = stride(c.n);
               c.off = off;
-              for (int jj = 0; jj < c.n; ++jj) {
-                qoff.push_back(off + jj);
-                qcp.push_back(c.cp);
-              }
               off += (long long)kSlots * c.cp;
               chunks.push_back(c);
             }
@@ -673,6 +778,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           boxes.push_back(b);
         }
   m->nbox = (int)boxes.size();
+  m->nchunk = (int)chunks.size();
   m->boxes_h = boxes;
   m->fcount = foff;
   m->max_pad = 0;
@@ -689,11 +795,13 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->perm, perm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->iperm, iperm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->lptr, lptr.size() * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&m->qoff, qoff.size() * sizeof(long long)) != cudaSuccess ||
-      cudaMalloc(&m->qcp, qcp.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&m->Fpm, pmoff * esz) != cudaSuccess ||
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
       cudaMalloc(&m->uptr, T.uptr.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->upd, T.upd.size() * sizeof(short2)) != cudaSuccess ||
+      cudaMalloc(&m->tgts, T.tgts.size() * sizeof(short4)) != cudaSuccess ||
+      cudaMalloc(&m->cons, T.cons.size() * sizeof(short2)) != cudaSuccess ||
+      cudaMalloc(&m->lslots, T.lslots.size() * sizeof(short)) != cudaSuccess ||
       cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * esz) != cudaSuccess ||
       cudaMalloc(&m->status, sizeof(int)) != cudaSuccess)
     return fail(KKT_ERR_NOMEM, "device allocation failed");
@@ -702,11 +810,17 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (e == cudaSuccess) e = cudaMemcpy(m->perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->lptr, lptr.data(), lptr.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->qoff, qoff.data(), qoff.size() * sizeof(long long), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->qcp, qcp.data(), qcp.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->uptr, T.uptr.data(), T.uptr.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->upd, T.upd.data(), T.upd.size() * sizeof(short2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<short2> gt(T.upd.size());
+    for (int q = 0; q < kSlots; ++q)
+      for (int k = T.uptr[q]; k < T.uptr[q + 1]; ++k) gt[k] = make_short2((short)q, T.upd[k].x);
+    e = cudaMemcpy(m->upd, gt.data(), gt.size() * sizeof(short2), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(m->tgts, T.tgts.data(), T.tgts.size() * sizeof(short4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->cons, T.cons.data(), T.cons.size() * sizeof(short2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->lslots, T.lslots.data(), T.lslots.size() * sizeof(short), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
@@ -724,13 +838,35 @@ namespace {
 
 template <typename T>
 kkt_status launch_factor(ras_precond* m, cudaStream_t s) {
-  const int warps = sizeof(T) == 8 ? 8 : 16;
-  const int nupd = (int)tables().upd.size();
-  const size_t smem = FactorSmem<T>::bytes(warps, nupd);
+  const SlotTables& tb = tables();
+  FactorSchedule sched{};
+  sched.gtab = m->upd;
+  sched.tgts = m->tgts;
+  sched.cons = m->cons;
+  sched.lslots = m->lslots;
+  sched.ntgts = (int)tb.tgts.size();
+  sched.nlslots = (int)tb.lslots.size();
+  sched.ncons = (int)tb.cons.size();
+  for (int c = 0; c < 3; ++c) {
+    sched.nlev[c] = tb.nlev[c];
+    sched.lev_base[c] = tb.lev_base[c];
+    sched.ebase[c] = tb.uptr[tb.base[c]];
+    sched.eend[c] = tb.uptr[tb.diag[c]];
+  }
+  for (size_t l = 0; l < tb.lptr_lev.size(); ++l) {
+    sched.lptr[l] = tb.lptr_lev[l];
+    sched.tptr[l] = tb.tptr_lev[l];
+  }
+  int warps = 32;
+  size_t smem = FactorLayout(warps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T)).total;
+  while (smem > 227 * 1024) smem = FactorLayout(--warps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T)).total;
   KKT_TRY_CUDA(cudaFuncSetAttribute(ilu0_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ilu0_factor<T><<<m->nbox, 32 * warps, smem, s>>>(m->boxes, m->perm, m->iperm, m->lptr, m->qoff, m->qcp, m->uptr,
-                                                   m->upd, nupd, (T*)m->F, m->status);
-  KKT_COUNT(1);
+  ilu0_factor<T><<<m->nbox, 32 * warps, smem, s>>>(m->boxes, m->perm, m->iperm, m->lptr, sched, (T*)m->Fpm,
+                                                   m->status);
+  const size_t tsmem = (size_t)ChunkCfg<T>::CH * kSlots * sizeof(T);
+  KKT_TRY_CUDA(cudaFuncSetAttribute(chunk_transpose<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+  chunk_transpose<T><<<m->nchunk, 256, tsmem, s>>>(m->boxes, m->chunks, (const T*)m->Fpm, (T*)m->F);
+  KKT_COUNT(2);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
@@ -762,11 +898,11 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   dim3 g(152, m->nbox);
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
   if (m->prec == 64) {
-    gather_matrix<double><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->qoff, m->qcp, (double*)m->F);
+    gather_matrix<double><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, (double*)m->Fpm);
     KKT_COUNT(1);
     KKT_TRY(launch_factor<double>(m, s));
   } else {
-    gather_matrix<float><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->qoff, m->qcp, (float*)m->F);
+    gather_matrix<float><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, (float*)m->Fpm);
     KKT_COUNT(1);
     KKT_TRY(launch_factor<float>(m, s));
   }
@@ -861,9 +997,11 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->lptr);
   cudaFree(m->uptr);
   cudaFree(m->upd);
-  cudaFree(m->qoff);
-  cudaFree(m->qcp);
+  cudaFree(m->Fpm);
   cudaFree(m->chunks);
+  cudaFree(m->tgts);
+  cudaFree(m->cons);
+  cudaFree(m->lslots);
   cudaFree(m->F);
   cudaFree(m->V);
   cudaFree(m->status);

@@ -12,7 +12,7 @@ struct Chunk {
   int q0;                      // first point (wavefront order, box-local)
   int n;                       // points
   int cp;                      // row stride of the block
-  int pad_;
+  int box;                     // owning box
   long long off;               // element offset of the block within the box
 };
 
@@ -23,7 +23,8 @@ struct BoxDesc {
   int ox0, ox1, oy0, oy1, oz0, oz1, ot0, ot1;   // owned ranges (global, half open)
   int nlev;                    // wavefronts x + 2y + 4z + 8t
   long long P;                 // points of the extended box
-  long long foff;              // offset of the box's factor values (elements)
+  long long foff;              // offset of the box's chunk blocks (elements)
+  long long pmoff;             // offset of the box's point-major factor values (elements)
   long long voff;              // offset of the box's padded local vector (elements)
   long long poff;              // offset into perm / iperm
   long long loff;              // offset into the wavefront pointers
@@ -43,9 +44,12 @@ struct ras_precond {
   int* lptr = nullptr;         // wavefront pointers per box (nlev + 1 each)
   int* uptr = nullptr;         // factorisation update lists
   short2* upd = nullptr;
-  long long* qoff = nullptr;   // per point: offset of its column in its chunk block
-  int* qcp = nullptr;          // per point: row stride of its chunk block
   Chunk* chunks = nullptr;
+  int nchunk = 0;
+  void* Fpm = nullptr;         // point-major factor values (factorisation)
+  short4* tgts = nullptr;      // factorisation level schedule
+  short2* cons = nullptr;
+  short* lslots = nullptr;
   void* F = nullptr;           // factor values
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;

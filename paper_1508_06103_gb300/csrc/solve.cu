@@ -28,6 +28,9 @@ struct coarse_level {
   double c_rtol = 0.1;
   int c_maxit = 4;
   double *rc = nullptr, *yc = nullptr, *y = nullptr, *t = nullptr;
+  int prec = 64;                     // precision of everything inside the preconditioner
+  float *cx32 = nullptr, *cy32 = nullptr;   // coarse FP32 scratch
+  float *fx32 = nullptr, *fy32 = nullptr;   // fine FP32 scratch
   GmresWork ws;
   int last_coarse_iters = 0;
 };
@@ -120,12 +123,26 @@ __global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt
 
 Grid4 grid_of(const kkt_problem* p) { return Grid4{p->nx, p->ny, p->nz, p->L, p->N}; }
 
+// The outer operator: FP64 KKT matvec (timed for the roofline report).
 struct KktOp : Operator {
   kkt_problem* p;
   explicit KktOp(kkt_problem* p_) : p(p_) {}
   kkt_status apply(const double* x, double* y, cudaStream_t s) override {
     TimedScope t(&p->mv_timing, s);
     return launch_matvec64(p->dev(), x, y, s);
+  }
+};
+
+// The coarse operator inside the preconditioner: FP64, or FP32 arithmetic on
+// FP64 vectors in the mixed form.
+struct CoarseOp : Operator {
+  kkt_problem* p;
+  int prec;
+  float *x32, *y32;
+  CoarseOp(kkt_problem* p_, int prec_, float* a, float* b) : p(p_), prec(prec_), x32(a), y32(b) {}
+  kkt_status apply(const double* x, double* y, cudaStream_t s) override {
+    if (prec == 64) return launch_matvec64(p->dev(), x, y, s);
+    return launch_matvec32_d(p->dev(), x, y, x32, y32, s);
   }
 };
 
@@ -142,7 +159,7 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   restrict_kernel<<<(unsigned)((pc->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
-  KktOp Ac(pc);
+  CoarseOp Ac(pc, c->prec, c->cx32, c->cy32);
   RasOp Mc(c->cras);
   GmresResult r;
   KKT_TRY(gmres_run(Ac, &Mc, c->rc, c->yc, c->ws, c->c_maxit, c->c_rtol, c->c_maxit, false, true, &r, s));
@@ -151,7 +168,8 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   interp_kernel<<<(unsigned)((pf->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
-  KKT_TRY(launch_residual(pf->dev(), x, c->y, c->t, s));   // t = x - F_h y
+  if (c->prec == 64) KKT_TRY(launch_residual(pf->dev(), x, c->y, c->t, s));   // t = x - F_h y
+  else KKT_TRY(launch_residual32(pf->dev(), x, c->y, c->t, c->fx32, c->fy32, s));
   KKT_TRY(ras_launch(fine, c->t, z, s));
   KKT_TRY(vec_axpby(z, 1.0, c->y, 1.0, pf->n, s));          // z = M^{-1} t + y
   return KKT_OK;
@@ -188,6 +206,7 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
   c->rt = fine->M / cnt;
   c->c_rtol = c_rtol;
   c->c_maxit = c_maxit;
+  c->prec = factor_prec == 32 ? 32 : 64;
   // coarse coefficients: cell means of the fine cells
   const int ncc = ccx * ccy * ccz;
   std::vector<double> ac(ncc, 0.0), vc(3 * (size_t)ncc, 0.0);
@@ -220,7 +239,11 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
       (cudaMalloc(&c->rc, c->cp->n * sizeof(double)) != cudaSuccess ||
        cudaMalloc(&c->yc, c->cp->n * sizeof(double)) != cudaSuccess ||
        cudaMalloc(&c->y, fine->n * sizeof(double)) != cudaSuccess ||
-       cudaMalloc(&c->t, fine->n * sizeof(double)) != cudaSuccess)) {
+       cudaMalloc(&c->t, fine->n * sizeof(double)) != cudaSuccess ||
+       (c->prec == 32 && (cudaMalloc(&c->cx32, c->cp->n * sizeof(float)) != cudaSuccess ||
+                          cudaMalloc(&c->cy32, c->cp->n * sizeof(float)) != cudaSuccess ||
+                          cudaMalloc(&c->fx32, fine->n * sizeof(float)) != cudaSuccess ||
+                          cudaMalloc(&c->fy32, fine->n * sizeof(float)) != cudaSuccess)))) {
     cudaGetLastError();
     set_error("coarse_setup: device allocation failed");
     st = KKT_ERR_NOMEM;
@@ -261,6 +284,10 @@ extern "C" void coarse_destroy(coarse_level* c) {
   cudaFree(c->yc);
   cudaFree(c->y);
   cudaFree(c->t);
+  cudaFree(c->cx32);
+  cudaFree(c->cy32);
+  cudaFree(c->fx32);
+  cudaFree(c->fy32);
   c->ws.release();
   delete c;
 }
