@@ -154,6 +154,26 @@ kkt_status ras_info(const ras_precond* m, int* nbox, long long* points, long lon
 kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream);
 
 /*
+ * ras_apply_static -- the same one-level RAS apply as ras_apply, for callers
+ *   that cannot call cudaMalloc: code running while another component owns the
+ *   device's memory pool, or a loop that must never trigger the device-wide
+ *   synchronisation an allocation can cause.  It allocates nothing: besides r,
+ *   z and the factors held by the handle, the only memory it touches is one
+ *   fixed 32 MiB array compiled into the library, which every GPU that loads
+ *   the library holds until the process exits.  (The paper has no counterpart;
+ *   this is an interface convenience.)
+ *   Limit: the padded local vectors of all subdomains must fit in the array,
+ *   i.e. 3 * sum over boxes of (lx+2)(ly+2)(lz+2)(lt+2) values of the factor
+ *   precision <= 32 MiB; larger handles get KKT_ERR_ARG (use ras_apply).
+ *   The first call on a device looks the array's device address up
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture.  Every call clears the part of the array it uses on
+ *   `stream` before the solve.  All calls share the one array, so calls whose
+ *   work overlaps on the GPU (other streams, other threads) race: order them.
+ */
+kkt_status ras_apply_static(ras_precond* m, const double* r, double* z, void* stream);
+
+/*
  * coarse_setup -- the coarse space-time level of the two-level method (Sec. 3.2):
  *   a nested coarse mesh of ccx x ccy x ccz cells and cnt steps (each must
  *   divide the fine one), rediscretised with cell-mean a and v and with each

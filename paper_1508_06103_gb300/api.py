@@ -122,6 +122,12 @@ class RAS:
     def refactor(self, stream=None) -> None:
         check(self._lib.ras_refactor(self.h, _stream(stream)), "ras_refactor")
 
+    def apply_static(self, r: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """ras_apply with the library's fixed scratch array (allocates nothing)."""
+        z = out if out is not None else torch.empty_like(r)
+        check(self._lib.ras_apply_static(self.h, _ptr(r), _ptr(z), _stream(stream)), "ras_apply_static")
+        return z
+
     def info(self):
         """dict(nbox, points, factor_values, value_bytes)."""
         nb, pts, fv, vb = C.c_int(), C.c_longlong(), C.c_longlong(), C.c_int()

@@ -51,6 +51,8 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -781,6 +783,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   m->nchunk = (int)chunks.size();
   m->boxes_h = boxes;
   m->fcount = foff;
+  m->vcount = voff;
   m->max_pad = 0;
   for (const BoxDesc& b : boxes)
     m->max_pad = std::max(m->max_pad, 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2));
@@ -872,18 +875,18 @@ kkt_status launch_factor(ras_precond* m, cudaStream_t s) {
 }
 
 template <typename T>
-kkt_status launch_solve(ras_precond* m, const double* r, double* z, cudaStream_t s) {
+kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaStream_t s) {
   const kkt_problem* p = m->prob;
   const int threads = ChunkCfg<T>::CH * kLanes;
   const size_t with_vec = solve_smem<T>(m->max_pad, true);
   if (with_vec <= kSmemLimit) {
     KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)with_vec));
-    ras_solve<T, true><<<m->nbox, threads, with_vec, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, (T*)m->V, r,
+    ras_solve<T, true><<<m->nbox, threads, with_vec, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r,
                                                           z, p->nx, p->ny, p->N, m->status);
   } else {
     const size_t smem = solve_smem<T>(m->max_pad, false);
     KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<T, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, (T*)m->V, r, z,
+    ras_solve<T, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r, z,
                                                        p->nx, p->ny, p->N, m->status);
   }
   KKT_COUNT(1);
@@ -918,8 +921,8 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
 
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s) {
   TimedScope timed(&m->timing, s);
-  if (m->prec == 64) return launch_solve<double>(m, r, z, s);
-  return launch_solve<float>(m, r, z, s);
+  if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s);
+  return launch_solve<float>(m, r, z, (float*)m->V, s);
 }
 
 kkt_status ras_check(ras_precond* m) {
@@ -1006,4 +1009,67 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->V);
   cudaFree(m->status);
   delete m;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free subdomain solve.  The padded local vectors the solve works
+// in come from a fixed array compiled into the library instead of the handle.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32u << 20;   // 32 MiB per device
+__device__ __align__(256) unsigned char g_ras_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {};
+
+// Device address of the static scratch on the current device, looked up once
+// per device (the host-side symbol is only a stand-in for it).
+kkt_status static_scratch(void** out) {
+  int dev = 0;
+  KKT_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("ras_apply_static: device ordinal out of range");
+    return KKT_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_ras_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+      set_error(std::string("ras_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return KKT_ERR_CUDA;
+    }
+    g_static_ptr[dev] = ptr;
+  }
+  *out = g_static_ptr[dev];
+  return KKT_OK;
+}
+
+}  // namespace
+
+extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* z, void* stream) {
+  if (!m || !r || !z) {
+    set_error("ras_apply_static: null argument");
+    return KKT_ERR_ARG;
+  }
+  if (r == z) {
+    set_error("ras_apply_static: r and z must not overlap");
+    return KKT_ERR_ARG;
+  }
+  const size_t bytes = (size_t)m->vcount * (m->prec == 64 ? sizeof(double) : sizeof(float));
+  if (bytes > kStaticScratchBytes) {
+    set_error("ras_apply_static: the subdomain local vectors need " + std::to_string(bytes) +
+              " bytes, more than the " + std::to_string(kStaticScratchBytes) +
+              "-byte static scratch; use ras_apply");
+    return KKT_ERR_ARG;
+  }
+  void* scratch = nullptr;
+  KKT_TRY(static_scratch(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  // the ghost layers of the local vectors must read zero; earlier calls (on
+  // any handle) may have left other data at those positions
+  KKT_TRY_CUDA(cudaMemsetAsync(scratch, 0, bytes, s));
+  if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)scratch, s);
+  return launch_solve<float>(m, r, z, (float*)scratch, s);
 }

@@ -37,6 +37,7 @@ struct ras_precond {
   int nbox = 0;
   long long fcount = 0;        // factor values
   long long max_pad = 0;       // largest padded local vector (elements)
+  long long vcount = 0;        // elements of all padded local vectors (the solve's scratch)
   std::vector<BoxDesc> boxes_h;
   BoxDesc* boxes = nullptr;
   int* perm = nullptr;         // wavefront order -> lexicographic local index
