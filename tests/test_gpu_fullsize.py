@@ -1,0 +1,101 @@
+"""Full-size GPU solves checked by properties the oracle evaluates at any size.
+
+* 32^3 cells x 64 steps (7,007,715 unknowns), two-level RAS, FGMRES(30):
+  the oracle's level-wise F_h gives the true relative residual of the GPU
+  solution, which must be <= 1e-8 (the stop test) in the FP64 and the mixed
+  form; the recovered sources of the two forms, solved to 1e-10, agree to
+  1e-5 relative L2 (the benchmark spec's bound for the mixed form).
+* 8^3 cells x 16 implicit-Euler steps (37,179 unknowns), one-level RAS
+  2x2x2x2, overlap 1: the GPU solution agrees with the oracle's solution of
+  the same system to 1e-8 relative after both are solved to 1e-13.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import forward as ofwd
+from oracle import kkt as okkt
+from oracle import krylov as okry
+from oracle import schwarz as osch
+from paper_1508_06103_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+OBS = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64.txt")
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1508_06103_gb300 import api as _api
+    from paper_1508_06103_gb300 import build
+
+    build.build()
+    return _api
+
+
+@pytest.fixture(scope="module")
+def mid_setup(api):
+    w = W.mid()
+    p = okkt.Problem.from_workload(w)
+    cobs = np.loadtxt(OBS, ndmin=2)
+    b = okkt.rhs(p, cobs)
+    prob = api.Problem.from_workload(w)
+    return w, p, cobs, b, prob
+
+
+def _solve(api, w, prob, cobs, prec, rtol):
+    ras = api.RAS(prob, w.nsub, w.overlap, prec)
+    co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, w.coarse_overlap, w.coarse_rtol, w.coarse_maxit, prec)
+    bd = prob.rhs(torch.from_numpy(cobs).cuda())
+    x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, coarse=co, restart=w.restart, rtol=rtol, maxit=2000)
+    f = prob.recover_source(x).cpu().numpy()
+    return x.cpu().numpy(), f, st, its, rel, bd.cpu().numpy()
+
+
+def test_rhs_full_size_matches_oracle(mid_setup):
+    w, p, cobs, b, prob = mid_setup
+    bd = prob.rhs(torch.from_numpy(cobs).cuda()).cpu().numpy()
+    assert np.allclose(bd, b, rtol=1e-14, atol=1e-18)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_two_level_solve_full_size_true_residual(api, mid_setup, prec):
+    w, p, cobs, b, prob = mid_setup
+    x, f, st, its, rel, bd = _solve(api, w, prob, cobs, prec, 1e-8)
+    assert st == 0 and rel <= 1e-8
+    r = b - okkt.apply(p, x)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b)
+    # the paper's qualitative claim: two-level needs several times fewer iterations
+    assert its <= 40
+
+
+def test_mixed_and_fp64_sources_agree_full_size(api, mid_setup):
+    w, p, cobs, b, prob = mid_setup
+    _, f64, st64, _, _, _ = _solve(api, w, prob, cobs, 64, 1e-10)
+    _, f32, st32, _, _, _ = _solve(api, w, prob, cobs, 32, 1e-10)
+    assert st64 == 0 and st32 == 0
+    assert np.linalg.norm(f32 - f64) <= 1e-5 * np.linalg.norm(f64)
+
+
+def test_tiny_implicit_euler_one_level_matches_oracle(api):
+    w = W.tiny(theta=1.0)
+    p = okkt.Problem.from_workload(w)
+    F = okkt.assemble(p)
+    C = ofwd.forward_march(p, w.true_source())
+    cobs = ofwd.observations(p, C, w.noise(), w.noise_eps)
+    b = okkt.rhs(p, cobs)
+    ref = osch.RAS(p, F, w.nsub, w.overlap, "lu")
+    sol = okry.gmres(lambda u: F @ u, b, ref.apply, restart=30, rtol=1e-13, maxit=400)
+    assert sol.converged
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, w.nsub, w.overlap, 64)
+    bd = prob.rhs(torch.from_numpy(cobs).cuda())
+    assert np.allclose(bd.cpu().numpy(), b, rtol=1e-14, atol=1e-18)
+    x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, restart=30, rtol=1e-13, maxit=3000)
+    assert st == 0
+    xe = x.cpu().numpy()
+    assert np.linalg.norm(xe - sol.x) <= 1e-8 * np.linalg.norm(sol.x)
