@@ -48,6 +48,7 @@ OBS_FILE = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64.t
 # time uses the same count.
 ORACLE_ITERATIONS = 23
 FALLBACK_HBM_GBS = 6800.0
+SLOTS_PER_POINT = 326   # stored ILU(0) values per space-time point (C, G, f rows: 108 + 56 + 162)
 
 
 def config_dict(w, extra=None):
@@ -313,7 +314,8 @@ def gpu_arm(args):
         ms = timed(lambda: step(ras, co, cobs), args.steps)
     api.timing_enable(False)
     launches = (api.launch_count() - launches0) // args.steps
-    ras_ms, ras_n = ras.timing()
+    ras_ms, ras_n = ras.timing(0)
+    fac_ms, fac_n = ras.timing(1)
     mv_ms, mv_n = api.matvec_timing(prob)
     mixed = dict(last)
     info = ras.info()
@@ -346,11 +348,30 @@ def gpu_arm(args):
     mv32_bytes = prob.n * 8 + coef_bytes * 4
 
     peak, peak_kind = measured_peaks()
-    # dominant kernel: the fine subdomain solve (ras_solve<float>)
-    ras_avg_ms = ras_ms / max(ras_n, 1)
-    ras_bytes = info["factor_values"] * info["value_bytes"] + info["points"] * 3 * 8 + prob.n * 8
-    achieved = ras_bytes / (ras_avg_ms * 1e-3) / 1e9
-    traffic = read_traffic("ras_solve")
+    traffic = {k: read_traffic(k) for k in ("ras_solve", "ilu0_factor", "matvec_tiled")}
+    # algorithmic bytes per launch (unpadded values)
+    vb = info["value_bytes"]
+    fvals = info["points"] * SLOTS_PER_POINT
+    kernels = {
+        "ilu0_factor": dict(desc="ILU(0) of all 256 fine subdomains, FP32 (refactorisation in every step)",
+                            ms=fac_ms, n=fac_n, bytes=2 * fvals * vb),
+        "ras_solve": dict(desc="fine subdomain ILU(0) solve, all 256 boxes, FP32 factors",
+                          ms=ras_ms, n=ras_n, bytes=fvals * vb + info["points"] * 3 * 8 + prob.n * 8),
+        "matvec_tiled": dict(desc="outer FP64 KKT matvec (FP64-pipe bound, see DESIGN.md)",
+                             ms=mv_ms, n=mv_n, bytes=mv64_bytes),
+    }
+    table = {}
+    for k, d in kernels.items():
+        avg = d["ms"] / max(d["n"], 1)
+        ach = d["bytes"] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        table[k] = {"kernel": d["desc"], "avg_launch_ms": avg, "launches_per_step": d["n"] / args.steps,
+                    "share_of_step": d["ms"] / args.steps / ms, "alg_bytes_per_launch": d["bytes"],
+                    "achieved_gbs": ach, "frac": ach / peak, "traffic": traffic[k]}
+    dom = max(table, key=lambda k: table[k]["share_of_step"])
+    roof = {"kernel": dom + ": " + table[dom]["kernel"], "bound": "hbm", "achieved": table[dom]["achieved_gbs"],
+            "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": table[dom]["frac"],
+            "traffic": table[dom]["traffic"], "alg_bytes_per_launch": table[dom]["alg_bytes_per_launch"],
+            "avg_launch_ms": table[dom]["avg_launch_ms"], "share_of_step": table[dom]["share_of_step"]}
 
     if rank != 0:
         return
@@ -368,12 +389,8 @@ def gpu_arm(args):
                    "fp64_frac": mv64_bytes / (mv64_ms * 1e-3) / 1e9 / peak,
                    "fp32_frac": mv32_bytes / (mv32_ms * 1e-3) / 1e9 / peak,
                    "bytes_fp64": mv64_bytes, "bytes_fp32": mv32_bytes},
-        "roofline": {"kernel": "ras_solve<float> (fine subdomain ILU(0) solve, all 256 boxes)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "alg_bytes_per_launch": ras_bytes,
-                     "avg_launch_ms": ras_avg_ms, "launches_per_step": ras_n / args.steps,
-                     "share_of_step": ras_ms / args.steps / ms},
-        "outer_matvec": {"avg_launch_ms": mv_ms / max(mv_n, 1), "launches_per_step": mv_n / args.steps},
+        "roofline": roof,
+        "kernels": table,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_ms / 1e3, "unit": UNIT, "h2d_bytes_per_step": cobs_np.size * 8,
                 "d2h_bytes_per_step": prob.levels * prob.N * 8},

@@ -232,13 +232,14 @@ kkt_status coarse_refactor(coarse_level* c, void* stream);
  * kkt_timing_read   -- accumulated event time (ms) and launch count of the FP64
  *                      matvecs issued by the solver on problem p (synchronises
  *                      on the recorded events).
- * ras_timing_read   -- the same for the subdomain-solve launches of RAS m.
+ * ras_timing_read   -- the same for launches of RAS m: kernel 0 = subdomain
+ *                      solve, 1 = ILU(0) factorisation.
  * kkt_timing_reset  -- clear the accumulators of p and m (either may be NULL).
  */
 long long kkt_launch_count(void);
 int kkt_timing_enable(int on);
 kkt_status kkt_timing_read(kkt_problem* p, double* total_ms, long long* launches);
-kkt_status ras_timing_read(ras_precond* m, double* total_ms, long long* launches);
+kkt_status ras_timing_read(ras_precond* m, int kernel, double* total_ms, long long* launches);
 kkt_status kkt_timing_reset(kkt_problem* p, ras_precond* m);
 
 /*

@@ -51,7 +51,7 @@ SIGNATURES = {
     "kkt_launch_count": (C.c_longlong, []),
     "kkt_timing_enable": (C.c_int, [C.c_int]),
     "kkt_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
-    "ras_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "ras_timing_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "kkt_timing_reset": (C.c_int, [C.c_void_p, C.c_void_p]),
     "kkt_destroy": (None, [C.c_void_p]),
     "ras_destroy": (None, [C.c_void_p]),

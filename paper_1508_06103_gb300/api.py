@@ -134,10 +134,10 @@ class RAS:
         check(self._lib.ras_info(self.h, C.byref(nb), C.byref(pts), C.byref(fv), C.byref(vb)), "ras_info")
         return dict(nbox=nb.value, points=pts.value, factor_values=fv.value, value_bytes=vb.value)
 
-    def timing(self):
-        """(total ms, launches) of the subdomain-solve kernel since the last reset."""
+    def timing(self, kernel: int = 0):
+        """(total ms, launches) since the last reset: kernel 0 subdomain solve, 1 factorisation."""
         ms, n = C.c_double(), C.c_longlong()
-        check(self._lib.ras_timing_read(self.h, C.byref(ms), C.byref(n)), "ras_timing_read")
+        check(self._lib.ras_timing_read(self.h, int(kernel), C.byref(ms), C.byref(n)), "ras_timing_read")
         return ms.value, n.value
 
     def close(self):

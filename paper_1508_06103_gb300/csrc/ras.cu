@@ -864,6 +864,7 @@ kkt_status launch_factor(ras_precond* m, cudaStream_t s) {
   size_t smem = FactorLayout(warps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T)).total;
   while (smem > 227 * 1024) smem = FactorLayout(--warps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T)).total;
   KKT_TRY_CUDA(cudaFuncSetAttribute(ilu0_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TimedScope timed(&m->factor_timing, s);
   ilu0_factor<T><<<m->nbox, 32 * warps, smem, s>>>(m->boxes, m->perm, m->iperm, m->lptr, sched, (T*)m->Fpm,
                                                    m->status);
   const size_t tsmem = (size_t)ChunkCfg<T>::CH * kSlots * sizeof(T);
@@ -975,20 +976,24 @@ extern "C" kkt_status ras_refactor(ras_precond* m, void* stream) {
   return ras_factor(m, (cudaStream_t)stream);
 }
 
-extern "C" kkt_status ras_timing_read(ras_precond* m, double* total_ms, long long* launches) {
-  if (!m) {
-    set_error("ras_timing_read: null argument");
+extern "C" kkt_status ras_timing_read(ras_precond* m, int kernel, double* total_ms, long long* launches) {
+  if (!m || (kernel != 0 && kernel != 1)) {
+    set_error("ras_timing_read: null handle or kernel not 0 (solve) / 1 (factorisation)");
     return KKT_ERR_ARG;
   }
-  m->timing.drain();
-  if (total_ms) *total_ms = m->timing.total_ms;
-  if (launches) *launches = m->timing.count;
+  TimingLog& log = kernel == 0 ? m->timing : m->factor_timing;
+  log.drain();
+  if (total_ms) *total_ms = log.total_ms;
+  if (launches) *launches = log.count;
   return KKT_OK;
 }
 
 extern "C" kkt_status kkt_timing_reset(kkt_problem* p, ras_precond* m) {
   if (p) p->mv_timing.reset();
-  if (m) m->timing.reset();
+  if (m) {
+    m->timing.reset();
+    m->factor_timing.reset();
+  }
   return KKT_OK;
 }
 

@@ -55,6 +55,7 @@ struct ras_precond {
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;
   TimingLog timing;            // subdomain-solve launches
+  TimingLog factor_timing;     // ILU(0) factorisation launches
 };
 
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
