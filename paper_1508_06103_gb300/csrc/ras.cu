@@ -67,24 +67,6 @@ struct SlotTables {
   // per slot (0..325): packed offsets
   int8_t dt[kSlots], dz[kSlots], dy[kSlots], dx[kSlots], comp[kSlots];
   int base[3], count[3], diag[3];       // diag = absolute slot index of the diagonal
-  // update lists of the factorisation, for every absolute L-slot s of each type:
-  // entries [uptr[s], uptr[s+1]) of (t, s2): a[s2] -= l * u_k[t]
-  std::vector<int> uptr;
-  std::vector<short2> upd;
-  // Level schedule of the elimination of one row.  An L-slot's multiplier is
-  // final once every slot that updates it has been processed, so the L-slots
-  // of a row type split into dependency levels (16 / 7 / 16 for C / G / f
-  // instead of 80 / 14 / 81 sequential steps).  Per row type and level:
-  // the slots whose multiplier is formed (lslots) and the update targets, each
-  // with the range of its contributions (s, e): a[s2] -= sum l_s * u_e.
-  std::vector<int> lev_ptr[3];        // level -> range in lslots / tgts (two entries per level)
-  std::vector<short> lslots;
-  std::vector<int> tptr_lev;          // per level of every row type: range of targets
-  std::vector<short4> tgts;           // (s2, contribution begin, end, 0)
-  std::vector<short2> cons;           // (slot s, update index e)
-  int nlev[3];
-  int lev_base[3];                    // first level index of each row type in tptr_lev / lptr_lev
-  std::vector<int> lptr_lev;          // per level: range in lslots
 };
 
 SlotTables build_tables() {
@@ -111,59 +93,6 @@ SlotTables build_tables() {
             }
     T.count[c] = s - T.base[c];
   }
-  // lookup (type c, offset, comp) -> slot
-  auto find = [&](int c, int dt, int dz, int dy, int dx, int cc) {
-    for (int q = T.base[c]; q < T.base[c] + T.count[c]; ++q)
-      if (T.dt[q] == dt && T.dz[q] == dz && T.dy[q] == dy && T.dx[q] == dx && T.comp[q] == cc) return q;
-    return -1;
-  };
-  T.uptr.assign(kSlots + 1, 0);
-  std::vector<std::vector<short2>> lists(kSlots);
-  for (int c = 0; c < 3; ++c)
-    for (int q = T.base[c]; q < T.diag[c]; ++q) {    // L-slots of row type c
-      const int ck = T.comp[q];                        // row type of the pivot row k
-      for (int t = T.diag[ck] + 1; t < T.base[ck] + T.count[ck]; ++t) {   // U-slots of row k
-        const int s2 = find(c, T.dt[q] + T.dt[t], T.dz[q] + T.dz[t], T.dy[q] + T.dy[t], T.dx[q] + T.dx[t], T.comp[t]);
-        if (s2 >= 0) lists[q].push_back(make_short2((short)t, (short)s2));
-      }
-    }
-  for (int q = 0; q < kSlots; ++q) T.uptr[q + 1] = T.uptr[q] + (int)lists[q].size();
-  for (int q = 0; q < kSlots; ++q) T.upd.insert(T.upd.end(), lists[q].begin(), lists[q].end());
-  // dependency levels of the L-slots and the pull-form update lists per level
-  int glev = 0;
-  T.lptr_lev.push_back(0);
-  T.tptr_lev.push_back(0);
-  for (int c = 0; c < 3; ++c) {
-    std::vector<int> lev(kSlots, 0);
-    int depth = 0;
-    for (int q = T.base[c]; q < T.diag[c]; ++q) {
-      int d = 0;
-      for (int p2 = T.base[c]; p2 < q; ++p2)
-        for (int e = T.uptr[p2]; e < T.uptr[p2 + 1]; ++e)
-          if (T.upd[e].y == q) d = std::max(d, lev[p2] + 1);
-      lev[q] = d;
-      depth = std::max(depth, d + 1);
-    }
-    T.nlev[c] = depth;
-    T.lev_base[c] = glev;
-    for (int l = 0; l < depth; ++l, ++glev) {
-      for (int q = T.base[c]; q < T.diag[c]; ++q)
-        if (lev[q] == l) T.lslots.push_back((short)q);
-      T.lptr_lev.push_back((int)T.lslots.size());
-      // targets of the updates issued by this level's slots
-      std::vector<std::vector<short2>> by_target(kSlots);
-      for (int q = T.base[c]; q < T.diag[c]; ++q)
-        if (lev[q] == l)
-          for (int e = T.uptr[q]; e < T.uptr[q + 1]; ++e) by_target[T.upd[e].y].push_back(make_short2((short)q, (short)e));
-      for (int s2 = 0; s2 < kSlots; ++s2)
-        if (!by_target[s2].empty()) {
-          const short b0 = (short)T.cons.size();
-          T.cons.insert(T.cons.end(), by_target[s2].begin(), by_target[s2].end());
-          T.tgts.push_back(make_short4((short)s2, b0, (short)T.cons.size(), 0));
-        }
-      T.tptr_lev.push_back((int)T.tgts.size());
-    }
-  }
   return T;
 }
 
@@ -183,9 +112,6 @@ constexpr int kGBase = 108, kGDiag = 122, kGEnd = 164;
 constexpr int kFBase = 164, kFDiag = 245, kFEnd = 326;
 constexpr int kLRanks = 175;        // L-slots of the three rows
 constexpr int kURanks = 151;        // diagonals and U-slots of the three rows
-constexpr int kMaxRow = 162;        // slots of the longest row (f)
-constexpr int kMaxUpd = 2320;       // factorisation updates of the longest row (f)
-constexpr int kMaxL = 81;           // L-slots of the longest row (f)
 
 // rank of slot s in a chunk block: L-slots of C, G, f, then diag+U of C, G, f
 int slot_rank(int s) {
@@ -222,212 +148,177 @@ int chunk_stride(int n) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// The factorisation works on a point-major copy of the values (all 326 slots of
-// a point contiguous, points in wavefront order), which keeps the U rows a
-// row is eliminated with in a few cache lines; a transpose then writes the
+template <typename T>
+struct Coefs {
+  const T *S, *ST, *B, *K;
+};
+template <typename T>
+__device__ __forceinline__ Coefs<T> coefs(const DevProblem& p);
+template <>
+__device__ __forceinline__ Coefs<double> coefs<double>(const DevProblem& p) {
+  return {p.S, p.ST, p.B, p.K};
+}
+template <>
+__device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
+  return {p.S32, p.ST32, p.B32, p.K32};
+}
+
+// The factorisation works on a level-major copy of the values: per box and
+// wavefront w a block [slot][point of the wavefront] (row stride = points of
+// the wavefront).  One thread eliminates the rows of one point, and threads
+// of consecutive points read the pivot rows of their neighbours at a common
+// offset from nearly consecutive addresses.  A transpose then writes the
 // chunk blocks the solve streams.
 
 // Fill the slot values of every point of every box from the stencil
-// coefficients: one warp per point, lanes over the slots (slot tables staged
-// in shared memory, as the lanes index them divergently).
+// coefficients: one thread per point, all threads of a warp on the same slot
+// (uniform table reads, and consecutive points of a wavefront write
+// consecutive addresses).  Entries are formed in the factor precision.
 template <typename T>
 __global__ void __launch_bounds__(256) gather_matrix(DevProblem p, const BoxDesc* __restrict__ boxes,
-                                                     const int* __restrict__ perm, T* __restrict__ Fpm) {
-  __shared__ int8_t sdt[kSlots], sdz[kSlots], sdy[kSlots], sdx[kSlots], scomp[kSlots];
-  for (int s = threadIdx.x; s < kSlots; s += blockDim.x) {
-    sdt[s] = c_dt[s];
-    sdz[s] = c_dz[s];
-    sdy[s] = c_dy[s];
-    sdx[s] = c_dx[s];
-    scomp[s] = c_comp[s];
-  }
-  __syncthreads();
+                                                     const int* __restrict__ perm, const int* __restrict__ lptr,
+                                                     const long long* __restrict__ levoff, T* __restrict__ Flev) {
   const BoxDesc bx = boxes[blockIdx.y];
-  T* Fb = Fpm + bx.pmoff;
-  const int lane = threadIdx.x & 31;
-  const double tau = p.tau, th = p.theta, th1 = 1.0 - p.theta;
-  for (long long q = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); q < bx.P;
-       q += (long long)gridDim.x * (blockDim.x >> 5)) {
-    const int lex = perm[bx.poff + q];
-    const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-    const int kt = lex / (bx.lx * bx.ly * bx.lz);
-    const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, n = bx.t0 + kt;
-    const int j = gx + p.nx * (gy + p.ny * gz);
-    const bool dirj = p.dir[j] != 0;
-    for (int s = lane; s < kSlots; s += 32) {
-      const int c = s < kGBase ? 0 : (s < kFBase ? 1 : 2);
-      const int dt = sdt[s], cc = scomp[s];
-      const int ax = kx + sdx[s], ay = ky + sdy[s], az = kz + sdz[s], at = kt + dt;
-      double v = 0.0;
-      if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
-        const int d = (sdx[s] + 1) + 3 * (sdy[s] + 1) + 9 * (sdz[s] + 1);
-        const size_t ci = (size_t)d * p.N + j;
-        if (c == 0) {
-          if (n == 0 || dirj) v = (s == kCDiag) ? 1.0 : 0.0;
-          else if (cc == 0) v = dt == 0 ? p.B[ci] + th * tau * p.S[ci] : -p.B[ci] + th1 * tau * p.S[ci];
-          else v = dt == 0 ? -th * tau * p.B[ci] : -th1 * tau * p.B[ci];
-        } else if (c == 1) {
-          if (n == p.M || dirj) v = (s == kGDiag) ? 1.0 : 0.0;
-          else if (cc == 1) v = dt == 0 ? p.B[ci] + th * tau * p.ST[ci] : -p.B[ci] + th1 * tau * p.ST[ci];
-          else v = (dt == 0 ? th1 : th) * tau * p.sens[j];
-        } else {
-          // f row: time mass / stiffness weights of the linear hats
-          double mt, lt;
-          if (dt == 0) {
-            mt = (n > 0 ? tau / 3 : 0.0) + (n < p.M ? tau / 3 : 0.0);
-            lt = (n > 0 ? 1.0 / tau : 0.0) + (n < p.M ? 1.0 / tau : 0.0);
-          } else {
-            mt = tau / 6;
-            lt = -1.0 / tau;
-          }
-          v = cc == 1 ? -mt * p.B[ci] : p.beta1 * lt * p.B[ci] + p.beta2 * mt * p.K[ci];
-        }
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= bx.P) return;
+  T* Fb = Flev + bx.pmoff;
+  const int* lp = lptr + bx.loff;
+  const Coefs<T> cf = coefs<T>(p);
+  const int lex = perm[bx.poff + q];
+  const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
+  const int kt = lex / (bx.lx * bx.ly * bx.lz);
+  const int w = kx + 2 * ky + 4 * kz + 8 * kt;
+  const int npts = lp[w + 1] - lp[w];
+  T* dst = Fb + levoff[bx.loff + w] + (q - lp[w]);
+  const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, n = bx.t0 + kt;
+  const int j = gx + p.nx * (gy + p.ny * gz);
+  const bool dirj = p.dir[j] != 0;
+  const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta), b1 = (T)p.beta1, b2 = (T)p.beta2;
+  const T sj = (T)p.sens[j];
+  // time weights of the f row at this level
+  const T mt0 = (n > 0 ? tau / (T)3 : (T)0) + (n < p.M ? tau / (T)3 : (T)0);
+  const T lt0 = (n > 0 ? (T)1 / tau : (T)0) + (n < p.M ? (T)1 / tau : (T)0);
+  const T mt1 = tau / (T)6, lt1 = -(T)1 / tau;
+  for (int s = 0; s < kSlots; ++s) {
+    const int dt = c_dt[s], cc = c_comp[s];
+    const int ax = kx + c_dx[s], ay = ky + c_dy[s], az = kz + c_dz[s], at = kt + dt;
+    T v = 0;
+    if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
+      const int d = (c_dx[s] + 1) + 3 * (c_dy[s] + 1) + 9 * (c_dz[s] + 1);
+      const size_t ci = (size_t)d * p.N + j;
+      if (s < kGBase) {
+        if (n == 0 || dirj) v = (s == kCDiag) ? (T)1 : (T)0;
+        else if (cc == 0) v = dt == 0 ? cf.B[ci] + th * tau * cf.S[ci] : -cf.B[ci] + th1 * tau * cf.S[ci];
+        else v = dt == 0 ? -th * tau * cf.B[ci] : -th1 * tau * cf.B[ci];
+      } else if (s < kFBase) {
+        if (n == p.M || dirj) v = (s == kGDiag) ? (T)1 : (T)0;
+        else if (cc == 1) v = dt == 0 ? cf.B[ci] + th * tau * cf.ST[ci] : -cf.B[ci] + th1 * tau * cf.ST[ci];
+        else v = (dt == 0 ? th1 : th) * tau * sj;
+      } else {
+        const T mt = dt == 0 ? mt0 : mt1, lt = dt == 0 ? lt0 : lt1;
+        v = cc == 1 ? -mt * cf.B[ci] : b1 * lt * cf.B[ci] + b2 * mt * cf.K[ci];
       }
-      Fb[q * kSlots + s] = (T)v;
     }
+    dst[(long long)s * npts] = v;
   }
 }
 
-// Chunk blocks [slot rank][cp] of the solve from the point-major factors;
-// one CTA per chunk, staged through shared memory so both sides are contiguous.
+// Chunk blocks [slot rank][cp] of the solve from the level-major factors; one
+// CTA per chunk, staged through shared memory so both sides are contiguous.
 template <typename T>
 __global__ void chunk_transpose(const BoxDesc* __restrict__ boxes, const Chunk* __restrict__ chunks,
-                                const T* __restrict__ Fpm, T* __restrict__ F) {
+                                const int* __restrict__ lptr, const long long* __restrict__ levoff,
+                                const T* __restrict__ Flev, T* __restrict__ F) {
   extern __shared__ __align__(128) unsigned char smem[];
-  T* tile = reinterpret_cast<T*>(smem);
+  T* tile = reinterpret_cast<T*>(smem);   // [slot][n]
   const Chunk c = chunks[blockIdx.x];
   const BoxDesc bx = boxes[c.box];
-  const T* src = Fpm + bx.pmoff + (long long)c.q0 * kSlots;
-  const int nin = c.n * kSlots;
-  for (int i = threadIdx.x; i < nin; i += blockDim.x) tile[i] = src[i];
+  const int* lp = lptr + bx.loff;
+  const int npts = lp[c.w + 1] - lp[c.w];
+  const T* src = Flev + bx.pmoff + levoff[bx.loff + c.w] + (c.q0 - lp[c.w]);
+  for (int i = threadIdx.x; i < c.n * kSlots; i += blockDim.x) {
+    const int s = i / c.n, jj = i - s * c.n;
+    tile[i] = src[(long long)s * npts + jj];
+  }
   __syncthreads();
   T* dst = F + bx.foff + c.off;
   const int nout = kSlots * c.cp;
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    const int r = o / c.cp, j = o - r * c.cp;
-    dst[o] = j < c.n ? tile[j * kSlots + c_slot_of_rank[r]] : (T)0;
+    const int r = o / c.cp, jj = o - r * c.cp;
+    dst[o] = jj < c.n ? tile[c_slot_of_rank[r] * c.n + jj] : (T)0;
   }
 }
 
 // ---------------------------------------------------------------------------
-// ILU(0) factorisation: one CTA per box, one warp per point of a wavefront.
-// For each row the warp first gathers into shared memory every value the
-// elimination of that row reads -- the pivots u_kk and the U entries u_kj of
-// the rows k it eliminates with -- with many independent loads in flight per
-// lane (consecutive lanes read consecutive entries of one pivot row), then
-// eliminates in shared memory by dependency level: at each level the row's
-// multipliers l_s = a_s / u_kk are formed, then a[s2] -= sum l_s u_k[t] over
-// the level's updates, one target per lane in a fixed order.
+// ILU(0) factorisation: one CTA per box, one thread per point of a
+// wavefront, rows C, G, f in turn.  The IKJ elimination of a row is the same
+// fixed sequence for every row of a type; ilu_rows.inc holds it as
+// straight-line code (row in registers, compile-time slot indices), and the
+// thread supplies where its pivot points' columns are.
 // ---------------------------------------------------------------------------
-struct FactorSchedule {
-  const short2* gtab;         // per update e: (L-slot s, U-slot t of the pivot row)
-  const short4* tgts;
-  const short2* cons;
-  const short* lslots;
-  int ntgts, nlslots, ncons;
-  int nlev[3], lev_base[3], ebase[3], eend[3];
-  int lptr[64], tptr[64];     // per global level: ranges in lslots / tgts (levels of C, G, f)
-};
+#include "ilu_rows.inc"
 
-// Shared-memory layout of the factor kernel: the tables, then one buffer per
-// warp (row values, gathered U entries, reciprocal pivots, neighbour positions).
-struct FactorLayout {
-  size_t gtab, cons, tgts, lsl, warp0, per_warp, total;
-  __host__ __device__ static size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
-  __host__ __device__ FactorLayout(int warps, int ncons, int ntgts, int nlslots, int tsize) {
-    gtab = 0;
-    cons = al(gtab + (size_t)ncons * 4, 8);
-    tgts = al(cons + (size_t)ncons * 4, 8);
-    lsl = tgts + (size_t)ntgts * 8;
-    warp0 = al(lsl + (size_t)nlslots * 2, 16);
-    per_warp = al((size_t)(kMaxRow + kMaxUpd + kMaxL) * tsize + kMaxL * 4, 16);
-    total = warp0 + (size_t)warps * per_warp;
+constexpr int kFactorThreads = 256;
+
+template <typename T, int C, int NSLOTS, int NNBR>
+__device__ __forceinline__ void factor_row(T* __restrict__ Fb, const int* __restrict__ iperm_b,
+                                           const int* __restrict__ lp, const long long* __restrict__ lo,
+                                           const BoxDesc& bx, int w, int own, int ost, int kx, int ky, int kz,
+                                           int kt, int* nb, int* ns, int* __restrict__ status) {
+  constexpr int base = C == 0 ? kCBase : (C == 1 ? kGBase : kFBase);
+  constexpr int diag = C == 0 ? kCDiag : (C == 1 ? kGDiag : kFDiag);
+  // where the pivot points' columns are (offset in Fb and row stride)
+#pragma unroll 1
+  for (int i = 0; i < NNBR; ++i) {
+    const int dt = c_gen_nbr[C][i][0], dz = c_gen_nbr[C][i][1], dy = c_gen_nbr[C][i][2], dx = c_gen_nbr[C][i][3];
+    const int ax = kx + dx, ay = ky + dy, az = kz + dz, at = kt + dt;
+    int off = -1, st = 0;
+    if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
+      const int qk = iperm_b[ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))];
+      const int wk = w + dx + 2 * dy + 4 * dz + 8 * dt;
+      off = (int)lo[wk] + (qk - lp[wk]);
+      st = lp[wk + 1] - lp[wk];
+    }
+    nb[i * kFactorThreads] = off;
+    ns[i * kFactorThreads] = st;
   }
-};
+  T a[NSLOTS];
+#pragma unroll
+  for (int i = 0; i < NSLOTS; ++i) a[i] = Fb[own + (long long)(base + i) * ost];
+  if (C == 0) ilu_elim_row0<T, kFactorThreads>(a, Fb, nb, ns);
+  if (C == 1) ilu_elim_row1<T, kFactorThreads>(a, Fb, nb, ns);
+  if (C == 2) ilu_elim_row2<T, kFactorThreads>(a, Fb, nb, ns);
+#pragma unroll
+  for (int i = 0; i < NSLOTS; ++i) Fb[own + (long long)(base + i) * ost] = a[i];
+  const double d = (double)a[diag - base];
+  if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
+}
 
 template <typename T>
-__global__ void ilu0_factor(const BoxDesc* __restrict__ boxes, const int* __restrict__ perm,
-                            const int* __restrict__ iperm, const int* __restrict__ lptr, const FactorSchedule sched,
-                            T* __restrict__ Fpm, int* __restrict__ status) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const FactorLayout lay(nwarps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T));
-  short2* gtab = reinterpret_cast<short2*>(smem + lay.gtab);
-  short2* cons = reinterpret_cast<short2*>(smem + lay.cons);
-  short4* tgts = reinterpret_cast<short4*>(smem + lay.tgts);
-  short* lsl = reinterpret_cast<short*>(smem + lay.lsl);
-  T* rowb = reinterpret_cast<T*>(smem + lay.warp0 + (size_t)warp * lay.per_warp);
-  T* gath = rowb + kMaxRow;
-  T* piv = gath + kMaxUpd;
-  int* kqs = reinterpret_cast<int*>(piv + kMaxL);
-  for (int i = threadIdx.x; i < sched.ncons; i += blockDim.x) {
-    gtab[i] = sched.gtab[i];
-    cons[i] = sched.cons[i];
-  }
-  for (int i = threadIdx.x; i < sched.ntgts; i += blockDim.x) tgts[i] = sched.tgts[i];
-  for (int i = threadIdx.x; i < sched.nlslots; i += blockDim.x) lsl[i] = sched.lslots[i];
-  __syncthreads();
-
+__global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* __restrict__ boxes,
+                                                                 const int* __restrict__ perm,
+                                                                 const int* __restrict__ iperm,
+                                                                 const int* __restrict__ lptr,
+                                                                 const long long* __restrict__ levoff,
+                                                                 T* __restrict__ Flev, int* __restrict__ status) {
+  __shared__ int nbs[kGenMaxNbrs * kFactorThreads], nss[kGenMaxNbrs * kFactorThreads];
   const BoxDesc bx = boxes[blockIdx.x];
-  T* Fb = Fpm + bx.pmoff;
+  T* Fb = Flev + bx.pmoff;
   const int* lp = lptr + bx.loff;
-  const int rbase[3] = {kCBase, kGBase, kFBase}, rdiag[3] = {kCDiag, kGDiag, kFDiag}, rend[3] = {kCEnd, kGEnd, kFEnd};
+  const long long* lo = levoff + bx.loff;
+  const int* ip = iperm + bx.poff;
+  int* nb = nbs + threadIdx.x;
+  int* ns = nss + threadIdx.x;
   for (int w = 0; w < bx.nlev; ++w) {
-    for (int q = lp[w] + warp; q < lp[w + 1]; q += nwarps) {
-      const int lex = perm[bx.poff + q];
+    const int npts = lp[w + 1] - lp[w];
+    for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+      const int lex = perm[bx.poff + lp[w] + j];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      for (int c = 0; c < 3; ++c) {
-        const int base = rbase[c], dg = rdiag[c], end = rend[c];
-        const int e0 = sched.ebase[c], e1 = sched.eend[c];
-        // 1. neighbour positions and reciprocal pivots of the L-slots; the row itself
-#pragma unroll 3
-        for (int s = base + lane; s < dg; s += 32) {
-          const int ax = kx + c_dx[s], ay = ky + c_dy[s], az = kz + c_dz[s], at = kt + c_dt[s];
-          int kq = -1;
-          if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt)
-            kq = iperm[bx.poff + ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))];
-          kqs[s - base] = kq;
-          piv[s - base] = kq >= 0 ? (T)1 / Fb[(long long)kq * kSlots + c_diag[c_comp[s]]] : (T)1;
-        }
-#pragma unroll 6
-        for (int i = lane; i < end - base; i += 32) rowb[i] = Fb[(long long)q * kSlots + base + i];
-        __syncwarp();
-        // 2. every u_kj the elimination reads (0 where the pivot row is outside the box)
-#pragma unroll 8
-        for (int e = e0 + lane; e < e1; e += 32) {
-          const short2 g = gtab[e];
-          const int kq = kqs[g.x - base];
-          gath[e - e0] = kq >= 0 ? Fb[(long long)kq * kSlots + g.y] : (T)0;
-        }
-        __syncwarp();
-        // 3. elimination by dependency level, in shared memory (piv holds 1 / u_kk);
-        //    a slot whose column leaves the box has value 0 and gathered entries 0
-        for (int l = sched.lev_base[c]; l < sched.lev_base[c] + sched.nlev[c]; ++l) {
-          for (int i = sched.lptr[l] + lane; i < sched.lptr[l + 1]; i += 32) {
-            const int sl = lsl[i] - base;
-            rowb[sl] *= piv[sl];
-          }
-          __syncwarp();
-          for (int i = sched.tptr[l] + lane; i < sched.tptr[l + 1]; i += 32) {
-            const short4 tg = tgts[i];
-            T acc = 0;
-            for (int k = tg.y; k < tg.z; ++k) {
-              const short2 cn = cons[k];
-              acc += rowb[cn.x - base] * gath[cn.y - e0];
-            }
-            rowb[tg.x - base] -= acc;
-          }
-          __syncwarp();
-        }
-        // 4. write back and check the pivot
-        for (int i = lane; i < end - base; i += 32) Fb[(long long)q * kSlots + base + i] = rowb[i];
-        if (lane == 0) {
-          const double d = (double)rowb[dg - base];
-          if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
-        }
-        __syncwarp();
-      }
+      const int own = (int)lo[w] + j;
+      factor_row<T, 0, kGenRowSlots0, kGenRowNbrs0>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, nb, ns, status);
+      factor_row<T, 1, kGenRowSlots1, kGenRowNbrs1>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, nb, ns, status);
+      factor_row<T, 2, kGenRowSlots2, kGenRowNbrs2>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, nb, ns, status);
     }
     __syncthreads();
   }
@@ -677,9 +568,16 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     return KKT_ERR_ARG;
   }
   const SlotTables& T = tables();
-  if (T.lptr_lev.size() > 64 || T.cons.size() != T.upd.size()) {
-    set_error("ras_setup: internal factorisation schedule too large");
-    return KKT_ERR_ARG;
+  {
+    long long h = 0;
+    for (int i = 0; i < kSlots; ++i)
+      h = (h * 131 + (i + 1) * (T.dt[i] + 2) * 7 + (T.dz[i] + 2) * 11 + (T.dy[i] + 2) * 13 + (T.dx[i] + 2) * 17 +
+           T.comp[i] * 19) % 1000000007LL;
+    if (h != kGenSlotChecksum || kGenRowSlots0 != T.count[0] || kGenRowSlots1 != T.count[1] ||
+        kGenRowSlots2 != T.count[2]) {
+      set_error("ras_setup: generated elimination code does not match the slot tables");
+      return KKT_ERR_ARG;
+    }
   }
   if (T.base[0] != kCBase || T.diag[0] != kCDiag || T.base[1] != kGBase || T.diag[1] != kGDiag ||
       T.base[2] != kFBase || T.diag[2] != kFDiag || T.base[2] + T.count[2] != kFEnd) {
@@ -714,6 +612,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   std::vector<BoxDesc> boxes;
   std::vector<int> perm, iperm, lptr;
+  std::vector<long long> levoff;
   std::vector<Chunk> chunks;
   long long foff = 0, voff = 0, pmoff = 0;
   for (int it = 0; it < nsub[3]; ++it)
@@ -748,6 +647,13 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
                 for (int kx = 0; kx < b.lx; ++kx) cnt[kx + 2 * ky + 4 * kz + 8 * kt + 1]++;
           for (int w = 0; w < b.nlev; ++w) cnt[w + 1] += cnt[w];
           for (int w = 0; w <= b.nlev; ++w) lptr.push_back(cnt[w]);
+          {
+            long long acc = 0;
+            for (int w = 0; w <= b.nlev; ++w) {
+              levoff.push_back(acc);
+              if (w < b.nlev) acc += (long long)kSlots * (cnt[w + 1] - cnt[w]);
+            }
+          }
           std::vector<int> bp(b.P), bi(b.P);
           std::vector<int> fill(cnt.begin(), cnt.end() - 1);
           int lex = 0;
@@ -768,6 +674,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
             for (int q0 = cnt[w]; q0 < cnt[w + 1]; q0 += CH) {
               Chunk c{};
               c.box = (int)boxes.size();
+              c.w = w;
               c.q0 = q0;
               c.n = std::min(CH, cnt[w + 1] - q0);
               c.cp = stride(c.n);
@@ -799,12 +706,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->iperm, iperm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->lptr, lptr.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->Fpm, pmoff * esz) != cudaSuccess ||
+      cudaMalloc(&m->levoff, levoff.size() * sizeof(long long)) != cudaSuccess ||
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
-      cudaMalloc(&m->uptr, T.uptr.size() * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&m->upd, T.upd.size() * sizeof(short2)) != cudaSuccess ||
-      cudaMalloc(&m->tgts, T.tgts.size() * sizeof(short4)) != cudaSuccess ||
-      cudaMalloc(&m->cons, T.cons.size() * sizeof(short2)) != cudaSuccess ||
-      cudaMalloc(&m->lslots, T.lslots.size() * sizeof(short)) != cudaSuccess ||
       cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * esz) != cudaSuccess ||
       cudaMalloc(&m->status, sizeof(int)) != cudaSuccess)
     return fail(KKT_ERR_NOMEM, "device allocation failed");
@@ -813,17 +716,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (e == cudaSuccess) e = cudaMemcpy(m->perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->lptr, lptr.data(), lptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->levoff, levoff.data(), levoff.size() * sizeof(long long), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->uptr, T.uptr.data(), T.uptr.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    std::vector<short2> gt(T.upd.size());
-    for (int q = 0; q < kSlots; ++q)
-      for (int k = T.uptr[q]; k < T.uptr[q + 1]; ++k) gt[k] = make_short2((short)q, T.upd[k].x);
-    e = cudaMemcpy(m->upd, gt.data(), gt.size() * sizeof(short2), cudaMemcpyHostToDevice);
-  }
-  if (e == cudaSuccess) e = cudaMemcpy(m->tgts, T.tgts.data(), T.tgts.size() * sizeof(short4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->cons, T.cons.data(), T.cons.size() * sizeof(short2), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->lslots, T.lslots.data(), T.lslots.size() * sizeof(short), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
@@ -841,35 +736,15 @@ namespace {
 
 template <typename T>
 kkt_status launch_factor(ras_precond* m, cudaStream_t s) {
-  const SlotTables& tb = tables();
-  FactorSchedule sched{};
-  sched.gtab = m->upd;
-  sched.tgts = m->tgts;
-  sched.cons = m->cons;
-  sched.lslots = m->lslots;
-  sched.ntgts = (int)tb.tgts.size();
-  sched.nlslots = (int)tb.lslots.size();
-  sched.ncons = (int)tb.cons.size();
-  for (int c = 0; c < 3; ++c) {
-    sched.nlev[c] = tb.nlev[c];
-    sched.lev_base[c] = tb.lev_base[c];
-    sched.ebase[c] = tb.uptr[tb.base[c]];
-    sched.eend[c] = tb.uptr[tb.diag[c]];
+  {
+    TimedScope timed(&m->factor_timing, s);
+    ilu0_factor<T><<<m->nbox, kFactorThreads, 0, s>>>(m->boxes, m->perm, m->iperm, m->lptr, m->levoff, (T*)m->Fpm,
+                                                      m->status);
   }
-  for (size_t l = 0; l < tb.lptr_lev.size(); ++l) {
-    sched.lptr[l] = tb.lptr_lev[l];
-    sched.tptr[l] = tb.tptr_lev[l];
-  }
-  int warps = 32;
-  size_t smem = FactorLayout(warps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T)).total;
-  while (smem > 227 * 1024) smem = FactorLayout(--warps, sched.ncons, sched.ntgts, sched.nlslots, (int)sizeof(T)).total;
-  KKT_TRY_CUDA(cudaFuncSetAttribute(ilu0_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  TimedScope timed(&m->factor_timing, s);
-  ilu0_factor<T><<<m->nbox, 32 * warps, smem, s>>>(m->boxes, m->perm, m->iperm, m->lptr, sched, (T*)m->Fpm,
-                                                   m->status);
   const size_t tsmem = (size_t)ChunkCfg<T>::CH * kSlots * sizeof(T);
   KKT_TRY_CUDA(cudaFuncSetAttribute(chunk_transpose<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
-  chunk_transpose<T><<<m->nchunk, 256, tsmem, s>>>(m->boxes, m->chunks, (const T*)m->Fpm, (T*)m->F);
+  chunk_transpose<T><<<m->nchunk, 256, tsmem, s>>>(m->boxes, m->chunks, m->lptr, m->levoff, (const T*)m->Fpm,
+                                                   (T*)m->F);
   KKT_COUNT(2);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
@@ -899,14 +774,16 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaSt
 
 kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   const DevProblem dp = m->prob->dev();
-  dim3 g(152, m->nbox);
+  long long pmax = 0;
+  for (const BoxDesc& b : m->boxes_h) pmax = std::max(pmax, b.P);
+  dim3 g((unsigned)((pmax + 255) / 256), m->nbox);
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
   if (m->prec == 64) {
-    gather_matrix<double><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, (double*)m->Fpm);
+    gather_matrix<double><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->lptr, m->levoff, (double*)m->Fpm);
     KKT_COUNT(1);
     KKT_TRY(launch_factor<double>(m, s));
   } else {
-    gather_matrix<float><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, (float*)m->Fpm);
+    gather_matrix<float><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->lptr, m->levoff, (float*)m->Fpm);
     KKT_COUNT(1);
     KKT_TRY(launch_factor<float>(m, s));
   }
@@ -1003,13 +880,9 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->perm);
   cudaFree(m->iperm);
   cudaFree(m->lptr);
-  cudaFree(m->uptr);
-  cudaFree(m->upd);
   cudaFree(m->Fpm);
+  cudaFree(m->levoff);
   cudaFree(m->chunks);
-  cudaFree(m->tgts);
-  cudaFree(m->cons);
-  cudaFree(m->lslots);
   cudaFree(m->F);
   cudaFree(m->V);
   cudaFree(m->status);

@@ -13,6 +13,8 @@ struct Chunk {
   int n;                       // points
   int cp;                      // row stride of the block
   int box;                     // owning box
+  int w;                       // wavefront of the chunk
+  int pad_;
   long long off;               // element offset of the block within the box
 };
 
@@ -24,7 +26,7 @@ struct BoxDesc {
   int nlev;                    // wavefronts x + 2y + 4z + 8t
   long long P;                 // points of the extended box
   long long foff;              // offset of the box's chunk blocks (elements)
-  long long pmoff;             // offset of the box's point-major factor values (elements)
+  long long pmoff;             // offset of the box's level-major factor values (elements)
   long long voff;              // offset of the box's padded local vector (elements)
   long long poff;              // offset into perm / iperm
   long long loff;              // offset into the wavefront pointers
@@ -43,14 +45,10 @@ struct ras_precond {
   int* perm = nullptr;         // wavefront order -> lexicographic local index
   int* iperm = nullptr;        // lexicographic -> wavefront order
   int* lptr = nullptr;         // wavefront pointers per box (nlev + 1 each)
-  int* uptr = nullptr;         // factorisation update lists
-  short2* upd = nullptr;
   Chunk* chunks = nullptr;
   int nchunk = 0;
-  void* Fpm = nullptr;         // point-major factor values (factorisation)
-  short4* tgts = nullptr;      // factorisation level schedule
-  short2* cons = nullptr;
-  short* lslots = nullptr;
+  void* Fpm = nullptr;         // level-major factor values (factorisation)
+  long long* levoff = nullptr; // per box and wavefront: offset of its block in Fpm
   void* F = nullptr;           // factor values
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;
