@@ -11,8 +11,10 @@ is therefore the same fixed sequence of operations for every row of a type:
 
 This script writes that sequence out as device code with compile-time slot
 indices, so one thread eliminates one row with the row in registers and the
-pivot-row entries read straight from memory.  Rows of pivot points outside
-the subdomain box are skipped (their columns hold 0).
+pivot-row entries read straight from memory.  The code has no branches: a
+pivot point outside the subdomain box is pointed at a stored unit row (1 on
+the diagonals, 0 elsewhere), so its column (which holds 0) contributes
+nothing, and all loads can be issued early.
 
 The slot order here must equal the one the library builds at run time
 (ras.cu, build_tables); the generated header carries the per-type counts and
@@ -96,7 +98,7 @@ def generate() -> str:
                 if key in index:
                     ups.append((t, index[key] - base[c]))
             nupd += len(ups)
-            body.append(f"  if (nb[{i} * NS] >= 0) {{  // slot {s}: pivot row {'CGf'[ck]} at offset {(dt, dz, dy, dx)}")
+            body.append(f"  {{  // slot {s}: pivot row {'CGf'[ck]} at offset {(dt, dz, dy, dx)}")
             body.append(f"    const T* u = F + nb[{i} * NS];")
             body.append(f"    const int st = ns[{i} * NS];")
             body.append(f"    const T l = a[{ls}] / u[{diag[ck]} * st];")
@@ -109,7 +111,7 @@ def generate() -> str:
         out.append(f"constexpr int kGenRowSlots{c} = {count[c]};")
         out.append(f"constexpr int kGenRowNbrs{c} = {len(nbrs)};")
         out.append(f"constexpr int kGenRowUpdates{c} = {nupd};")
-        out.append("// nb[i * NS]: offset of pivot point i's column in F (-1 outside the box),")
+        out.append("// nb[i * NS]: offset of pivot point i's column in F (the unit row outside the box),")
         out.append("// ns[i * NS]: row stride of its level block")
         out.append("template <typename T, int NS>")
         out.append(f"__device__ __forceinline__ void ilu_elim_row{c}(T* a, const T* __restrict__ F, "

@@ -264,7 +264,7 @@ template <typename T, int C, int NSLOTS, int NNBR>
 __device__ __forceinline__ void factor_row(T* __restrict__ Fb, const int* __restrict__ iperm_b,
                                            const int* __restrict__ lp, const long long* __restrict__ lo,
                                            const BoxDesc& bx, int w, int own, int ost, int kx, int ky, int kz,
-                                           int kt, int* nb, int* ns, int* __restrict__ status) {
+                                           int kt, int unit_row, int* nb, int* ns, int* __restrict__ status) {
   constexpr int base = C == 0 ? kCBase : (C == 1 ? kGBase : kFBase);
   constexpr int diag = C == 0 ? kCDiag : (C == 1 ? kGDiag : kFDiag);
   // where the pivot points' columns are (offset in Fb and row stride)
@@ -272,7 +272,7 @@ __device__ __forceinline__ void factor_row(T* __restrict__ Fb, const int* __rest
   for (int i = 0; i < NNBR; ++i) {
     const int dt = c_gen_nbr[C][i][0], dz = c_gen_nbr[C][i][1], dy = c_gen_nbr[C][i][2], dx = c_gen_nbr[C][i][3];
     const int ax = kx + dx, ay = ky + dy, az = kz + dz, at = kt + dt;
-    int off = -1, st = 0;
+    int off = unit_row, st = 1;
     if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
       const int qk = iperm_b[ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))];
       const int wk = w + dx + 2 * dy + 4 * dz + 8 * dt;
@@ -309,6 +309,11 @@ __global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* 
   const int* ip = iperm + bx.poff;
   int* nb = nbs + threadIdx.x;
   int* ns = nss + threadIdx.x;
+  const int unit_row = (int)lo[bx.nlev];
+  // the unit row: 1 at the three diagonal slots, 0 elsewhere
+  for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
+    Fb[unit_row + s] = (s == kCDiag || s == kGDiag || s == kFDiag) ? (T)1 : (T)0;
+  __syncthreads();
   for (int w = 0; w < bx.nlev; ++w) {
     const int npts = lp[w + 1] - lp[w];
     for (int j = threadIdx.x; j < npts; j += blockDim.x) {
@@ -316,9 +321,9 @@ __global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* 
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
       const int own = (int)lo[w] + j;
-      factor_row<T, 0, kGenRowSlots0, kGenRowNbrs0>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, nb, ns, status);
-      factor_row<T, 1, kGenRowSlots1, kGenRowNbrs1>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, nb, ns, status);
-      factor_row<T, 2, kGenRowSlots2, kGenRowNbrs2>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, nb, ns, status);
+      factor_row<T, 0, kGenRowSlots0, kGenRowNbrs0>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, unit_row, nb, ns, status);
+      factor_row<T, 1, kGenRowSlots1, kGenRowNbrs1>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, unit_row, nb, ns, status);
+      factor_row<T, 2, kGenRowSlots2, kGenRowNbrs2>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, unit_row, nb, ns, status);
     }
     __syncthreads();
   }
@@ -448,7 +453,7 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
   }
   __syncthreads();
   const int lane = threadIdx.x & (kLanes - 1), j = threadIdx.x / kLanes;
-  // forward sweep with the unit lower factor; rows C, G, f of a point in turn
+  // forward sweep with the unit lower factor
   for (int i = 0; i < nch; ++i) {
     const int b = i & 1;
     if (threadIdx.x == 0) {
@@ -471,17 +476,24 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
       v1 = vp[1];
       v2 = vp[2];
     }
-    T acc = row_dot<0, 80, 0>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) vp[0] = v0 - acc;
-    __syncwarp();
-    acc = row_dot<80, 94, 28>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) vp[1] = v1 - acc;
-    __syncwarp();
-    acc = row_dot<94, 175, 70>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) vp[2] = v2 - acc;
+    // Every L-slot reads a point of an earlier wavefront except the G row's
+    // own-C slot (block row 93) and the f row's own-G slot (row 174), so the
+    // three rows' sums over other points are gathered together and the two
+    // own-point terms are applied afterwards in C, G, f order.
+    const T aC = row_dot<0, 80, 0>(B, c.cp, j, off, vp, lane, act);
+    const T aG = row_dot<80, 93, 28>(B, c.cp, j, off, vp, lane, act);
+    const T aF = row_dot<94, 174, 70>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) {
+      const T yc = v0 - aC;
+      const T yg = v1 - aG - B[93 * c.cp + j] * yc;
+      const T yf = v2 - aF - B[174 * c.cp + j] * yg;
+      vp[0] = yc;
+      vp[1] = yg;
+      vp[2] = yf;
+    }
     __syncthreads();
   }
-  // backward sweep with the upper factor; rows f, G, C of a point in turn
+  // backward sweep with the upper factor
   for (int k = 0; k < nch; ++k) {
     const int i = nch - 1 - k;
     const int b = (nch + k) & 1;
@@ -505,14 +517,19 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
       d1 = B[28 * c.cp + j];
       d2 = B[70 * c.cp + j];
     }
-    T acc = row_dot<71, 151, 175>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) vp[2] = (v2 - acc) / d2;
-    __syncwarp();
-    acc = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) vp[1] = (v1 - acc) / d1;
-    __syncwarp();
-    acc = row_dot<1, 28, 80>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) vp[0] = (v0 - acc) / d0;
+    // Every U-slot reads a point of a later wavefront except the C row's
+    // own-f slot (U block row 1), applied after the f row is solved.
+    const T bF = row_dot<71, 151, 175>(B, c.cp, j, off, vp, lane, act);
+    const T bG = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
+    const T bC = row_dot<2, 28, 80>(B, c.cp, j, off, vp, lane, act);
+    if (act && lane == 0) {
+      const T zf = (v2 - bF) / d2;
+      const T zg = (v1 - bG) / d1;
+      const T zc = (v0 - bC - B[1 * c.cp + j] * zf) / d0;
+      vp[0] = zc;
+      vp[1] = zg;
+      vp[2] = zf;
+    }
     __syncthreads();
   }
   // scatter the owned part: (R^0)^T
@@ -634,7 +651,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           b.nlev = (b.lx - 1) + 2 * (b.ly - 1) + 4 * (b.lz - 1) + 8 * (b.lt - 1) + 1;
           b.foff = foff;
           b.pmoff = pmoff;
-          pmoff += b.P * kSlots;
+          pmoff += b.P * kSlots + kSlots;     // + the unit row of pivot points outside the box
           b.voff = voff;
           b.poff = (long long)perm.size();
           b.loff = (long long)lptr.size();

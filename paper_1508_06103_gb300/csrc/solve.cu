@@ -41,7 +41,9 @@ struct Grid4 {
   int nx, ny, nz, L, N;
 };
 
-// fine y = I^h_c yc (multilinear in x, y, z, t); one thread per fine point
+// fine y = I^h_c yc (multilinear in x, y, z, t); one thread per fine point.
+// Per axis the fine index i = I r + rem takes (1 - rem/r) of coarse I and
+// rem/r of coarse I + 1 (the second weight is 0 on coarse points).
 __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ yc,
                               double* __restrict__ y) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -49,41 +51,37 @@ __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, 
   const int n = (int)(idx / f.N);
   const int j = (int)(idx - (long long)n * f.N);
   const int ix = j % f.nx, iy = (j / f.nx) % f.ny, iz = j / (f.nx * f.ny);
-  int I[4][2];
-  double W[4][2];
-  int cnt[4];
-  const int pos[4] = {ix, iy, iz, n}, rr[4] = {rx, ry, rz, rt}, cn[4] = {c.nx, c.ny, c.nz, c.L};
-  for (int a = 0; a < 4; ++a) {
-    const int q = pos[a] / rr[a], rem = pos[a] - q * rr[a];
-    I[a][0] = q;
-    if (rem == 0) {
-      W[a][0] = 1.0;
-      cnt[a] = 1;
-    } else {
-      W[a][0] = 1.0 - (double)rem / rr[a];
-      I[a][1] = min(q + 1, cn[a] - 1);
-      W[a][1] = (double)rem / rr[a];
-      cnt[a] = 2;
-    }
-  }
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (int at = 0; at < cnt[3]; ++at)
-    for (int az = 0; az < cnt[2]; ++az)
-      for (int ay = 0; ay < cnt[1]; ++ay)
-        for (int ax = 0; ax < cnt[0]; ++ax) {
-          const double w = W[0][ax] * W[1][ay] * W[2][az] * W[3][at];
-          const long long jc = I[0][ax] + (long long)c.nx * (I[1][ay] + (long long)c.ny * I[2][az]);
-          const double* src = yc + 3 * ((long long)I[3][at] * c.N + jc);
-          acc[0] += w * src[0];
-          acc[1] += w * src[1];
-          acc[2] += w * src[2];
+  const int X0 = ix / rx, Y0 = iy / ry, Z0 = iz / rz, T0 = n / rt;
+  const double wx = (double)(ix - X0 * rx) / rx, wy = (double)(iy - Y0 * ry) / ry;
+  const double wz = (double)(iz - Z0 * rz) / rz, wt = (double)(n - T0 * rt) / rt;
+  const int X1 = wx > 0 ? X0 + 1 : X0, Y1 = wy > 0 ? Y0 + 1 : Y0, Z1 = wz > 0 ? Z0 + 1 : Z0, T1 = wt > 0 ? T0 + 1 : T0;
+  const int xs[2] = {X0, X1}, ys[2] = {Y0, Y1}, zs[2] = {Z0, Z1}, ts[2] = {T0, T1};
+  const double wxs[2] = {1.0 - wx, wx}, wys[2] = {1.0 - wy, wy}, wzs[2] = {1.0 - wz, wz}, wts[2] = {1.0 - wt, wt};
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+  for (int at = 0; at < 2; ++at)
+#pragma unroll
+    for (int az = 0; az < 2; ++az)
+#pragma unroll
+      for (int ay = 0; ay < 2; ++ay) {
+        const double w3 = wts[at] * wzs[az] * wys[ay];
+        const double* src = yc + 3 * ((long long)ts[at] * c.N + c.nx * (ys[ay] + c.ny * zs[az]));
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax) {
+          const double w = w3 * wxs[ax];
+          const double* q = src + 3 * xs[ax];
+          a0 += w * q[0];
+          a1 += w * q[1];
+          a2 += w * q[2];
         }
-  y[3 * idx] = acc[0];
-  y[3 * idx + 1] = acc[1];
-  y[3 * idx + 2] = acc[2];
+      }
+  y[3 * idx] = a0;
+  y[3 * idx + 1] = a1;
+  y[3 * idx + 2] = a2;
 }
 
-// coarse rc = (I^h_c)^T x; one thread per coarse point gathers its fine support
+// coarse rc = (I^h_c)^T x; one thread per coarse point gathers its fine
+// support: fine index I r + a, |a| < r, weight 1 - |a|/r per axis.
 __global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ x,
                                 double* __restrict__ rc) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -91,34 +89,32 @@ __global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt
   const int n = (int)(idx / c.N);
   const int j = (int)(idx - (long long)n * c.N);
   const int I = j % c.nx, J = (j / c.nx) % c.ny, K = j / (c.nx * c.ny);
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (int at = -rt + 1; at <= rt - 1; ++at) {
-    const int ft = n * rt + at;
-    if (ft < 0 || ft >= f.L) continue;
-    const double wt = 1.0 - (double)abs(at) / rt;
-    for (int az = -rz + 1; az <= rz - 1; ++az) {
-      const int fz = K * rz + az;
-      if (fz < 0 || fz >= f.nz) continue;
-      const double wz = wt * (1.0 - (double)abs(az) / rz);
-      for (int ay = -ry + 1; ay <= ry - 1; ++ay) {
-        const int fy = J * ry + ay;
-        if (fy < 0 || fy >= f.ny) continue;
-        const double wy = wz * (1.0 - (double)abs(ay) / ry);
-        for (int ax = -rx + 1; ax <= rx - 1; ++ax) {
-          const int fx = I * rx + ax;
-          if (fx < 0 || fx >= f.nx) continue;
-          const double w = wy * (1.0 - (double)abs(ax) / rx);
-          const double* src = x + 3 * ((long long)ft * f.N + fx + (long long)f.nx * (fy + (long long)f.ny * fz));
-          acc[0] += w * src[0];
-          acc[1] += w * src[1];
-          acc[2] += w * src[2];
+  const int x0 = max(I * rx - rx + 1, 0), x1 = min(I * rx + rx - 1, f.nx - 1);
+  const int y0 = max(J * ry - ry + 1, 0), y1 = min(J * ry + ry - 1, f.ny - 1);
+  const int z0 = max(K * rz - rz + 1, 0), z1 = min(K * rz + rz - 1, f.nz - 1);
+  const int t0 = max(n * rt - rt + 1, 0), t1 = min(n * rt + rt - 1, f.L - 1);
+  const double irx = 1.0 / rx, iry = 1.0 / ry, irz = 1.0 / rz, irt = 1.0 / rt;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int ft = t0; ft <= t1; ++ft) {
+    const double wt = 1.0 - abs(ft - n * rt) * irt;
+    for (int fz = z0; fz <= z1; ++fz) {
+      const double wz = wt * (1.0 - abs(fz - K * rz) * irz);
+      for (int fy = y0; fy <= y1; ++fy) {
+        const double wy = wz * (1.0 - abs(fy - J * ry) * iry);
+        const double* row = x + 3 * ((long long)ft * f.N + f.nx * (fy + f.ny * fz));
+        for (int fx = x0; fx <= x1; ++fx) {
+          const double w = wy * (1.0 - abs(fx - I * rx) * irx);
+          const double* q = row + 3 * fx;
+          a0 += w * q[0];
+          a1 += w * q[1];
+          a2 += w * q[2];
         }
       }
     }
   }
-  rc[3 * idx] = acc[0];
-  rc[3 * idx + 1] = acc[1];
-  rc[3 * idx + 2] = acc[2];
+  rc[3 * idx] = a0;
+  rc[3 * idx + 1] = a1;
+  rc[3 * idx + 2] = a2;
 }
 
 Grid4 grid_of(const kkt_problem* p) { return Grid4{p->nx, p->ny, p->nz, p->L, p->N}; }
