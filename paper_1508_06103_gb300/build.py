@@ -34,16 +34,24 @@ def _flags():
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    # the factorisation units take longest: start them first
+    names = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    names.sort(key=lambda f: not f.startswith("factor"))
+    return [os.path.join(CSRC, f) for f in names]
 
 
 def _compile(src: str, verbose_ptxas: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
+    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".inc"))]
     deps.append(os.path.join(INCLUDE, "stkkt.h"))
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps) and not verbose_ptxas:
         return obj
     cmd = [nvcc(), "-c", src, "-o", obj] + _flags()
+    if os.path.basename(src).startswith("factor"):
+        # the generated elimination code is one long block of independent
+        # loads; at -O3 the LLVM optimiser moves them so far ahead that ptxas
+        # spills registers, at -O2 it leaves the scheduling to ptxas
+        cmd += ["-Xcicc", "-O2"]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     out = subprocess.run(cmd, capture_output=True, text=True)

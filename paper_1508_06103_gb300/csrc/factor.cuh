@@ -1,0 +1,183 @@
+// ILU(0) factorisation of all subdomain matrices (Sec. 3.2), in place on the
+// chunk layout that the subdomain solve streams.  Included by factor32.cu and
+// factor64.cu, one translation unit per precision (the generated elimination
+// code is large, and the two compile in parallel).
+//
+// Values.  gather_chunks forms every slot value of every box point from the
+// stencil coefficients (the principal submatrix of F_h on the extended box,
+// Eq. 10-12; a slot whose column leaves the box holds 0) and writes it to the
+// point's column of its chunk block, row c_gen_rank[slot].
+//
+// Elimination.  One CTA per box steps through the wavefronts
+// w = x + 2y + 4z + 8t with a barrier between them; one thread takes one point
+// of the wavefront and eliminates its C, G and f rows in turn with the
+// straight-line code of ilu_rows.inc.  The thread first lists where the
+// columns of its 41 possible pivot points are (offset and row stride of their
+// chunk blocks); a pivot point outside the box is sent to the box's unit row
+// (stride 1, 1 at the three diagonal ranks, 0 elsewhere).  The diagonal slot
+// of a finished row holds 1/u_kk.
+#pragma once
+
+#include "internal.cuh"
+#include "ras.cuh"
+
+namespace {
+
+#include "ilu_rows.inc"
+#include "ilu_slots.inc"
+
+static_assert(kGenSlots == kSlots, "slot count");
+
+template <typename T>
+struct Coefs {
+  const T *S, *ST, *B, *K;
+};
+template <typename T>
+__device__ __forceinline__ Coefs<T> coefs(const DevProblem& p);
+template <>
+__device__ __forceinline__ Coefs<double> coefs<double>(const DevProblem& p) {
+  return {p.S, p.ST, p.B, p.K};
+}
+template <>
+__device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
+  return {p.S32, p.ST32, p.B32, p.K32};
+}
+
+constexpr int kGatherThreads = 256;
+constexpr int kFactorThreads = 256;
+// diagonal slots of the C, G and f rows
+constexpr int kDiagC = 80, kDiagG = 122, kDiagF = 245;
+
+// One thread per point (wavefront order, so the threads of a chunk write
+// consecutive addresses); all threads of a warp on the same slot.  Entries are
+// formed in the factor precision.  Also writes each box's unit row.
+template <typename T>
+__global__ void __launch_bounds__(kGatherThreads) gather_chunks(DevProblem p, const BoxDesc* __restrict__ boxes,
+                                                                const int* __restrict__ perm,
+                                                                const int2* __restrict__ ptab, T* __restrict__ F) {
+  const BoxDesc bx = boxes[blockIdx.y];
+  T* Fb = F + bx.foff;
+  if (blockIdx.x == 0)
+    for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
+      Fb[bx.unit + c_gen_rank[s]] = (s == kDiagC || s == kDiagG || s == kDiagF) ? (T)1 : (T)0;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= bx.P) return;
+  const Coefs<T> cf = coefs<T>(p);
+  const int lex = perm[bx.poff + q];
+  const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
+  const int kt = lex / (bx.lx * bx.ly * bx.lz);
+  const int2 pt = ptab[bx.poff + q];
+  T* dst = Fb + pt.x;
+  const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, n = bx.t0 + kt;
+  const int j = gx + p.nx * (gy + p.ny * gz);
+  const bool dirj = p.dir[j] != 0;
+  const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta), b1 = (T)p.beta1, b2 = (T)p.beta2;
+  const T sj = (T)p.sens[j];
+  // time weights of the f row at this level
+  const T mt0 = (n > 0 ? tau / (T)3 : (T)0) + (n < p.M ? tau / (T)3 : (T)0);
+  const T lt0 = (n > 0 ? (T)1 / tau : (T)0) + (n < p.M ? (T)1 / tau : (T)0);
+  const T mt1 = tau / (T)6, lt1 = -(T)1 / tau;
+  for (int s = 0; s < kSlots; ++s) {
+    const int dt = c_gen_slot[s][0], dz = c_gen_slot[s][1], dy = c_gen_slot[s][2], dx = c_gen_slot[s][3];
+    const int cc = c_gen_slot[s][4];
+    const int ax = kx + dx, ay = ky + dy, az = kz + dz, at = kt + dt;
+    T v = 0;
+    if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
+      const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+      const size_t ci = (size_t)d * p.N + j;
+      if (s < kGenRowSlots0) {
+        if (n == 0 || dirj) v = (s == kDiagC) ? (T)1 : (T)0;
+        else if (cc == 0) v = dt == 0 ? cf.B[ci] + th * tau * cf.S[ci] : -cf.B[ci] + th1 * tau * cf.S[ci];
+        else v = dt == 0 ? -th * tau * cf.B[ci] : -th1 * tau * cf.B[ci];
+      } else if (s < kGenRowSlots0 + kGenRowSlots1) {
+        if (n == p.M || dirj) v = (s == kDiagG) ? (T)1 : (T)0;
+        else if (cc == 1) v = dt == 0 ? cf.B[ci] + th * tau * cf.ST[ci] : -cf.B[ci] + th1 * tau * cf.ST[ci];
+        else v = (dt == 0 ? th1 : th) * tau * sj;
+      } else {
+        const T mt = dt == 0 ? mt0 : mt1, lt = dt == 0 ? lt0 : lt1;
+        v = cc == 1 ? -mt * cf.B[ci] : b1 * lt * cf.B[ci] + b2 * mt * cf.K[ci];
+      }
+    }
+    dst[(long long)c_gen_rank[s] * pt.y] = v;
+  }
+}
+
+__device__ __forceinline__ void check_pivot(double d, int* status) {
+  if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* __restrict__ boxes,
+                                                                 const int* __restrict__ iperm,
+                                                                 const int* __restrict__ perm,
+                                                                 const int* __restrict__ lptr,
+                                                                 const int2* __restrict__ ptab, T* __restrict__ F,
+                                                                 int* __restrict__ status) {
+  // per thread and pivot point: {offset of its column in Fb, row stride of its block}
+  __shared__ int2 nbs[kGenNbrs * kFactorThreads];
+  const BoxDesc bx = boxes[blockIdx.x];
+  T* Fb = F + bx.foff;
+  const int* lp = lptr + bx.loff;
+  const int* ip = iperm + bx.poff;
+  const int2* pb = ptab + bx.poff;
+  int2* nb = nbs + threadIdx.x;
+  const int unit = (int)bx.unit;
+  for (int w = 0; w < bx.nlev; ++w) {
+    const int npts = lp[w + 1] - lp[w];
+    for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+      const int q = lp[w] + j;
+      const int lex = perm[bx.poff + q];
+      const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
+      const int kt = lex / (bx.lx * bx.ly * bx.lz);
+#pragma unroll 1
+      for (int i = 0; i < kGenNbrs; ++i) {
+        const int dt = c_gen_nbr[i][0], dz = c_gen_nbr[i][1], dy = c_gen_nbr[i][2], dx = c_gen_nbr[i][3];
+        const int ax = kx + dx, ay = ky + dy, az = kz + dz, at = kt + dt;
+        int2 e = make_int2(unit, 1);
+        if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt)
+          e = pb[ip[ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))]];
+        nb[i * kFactorThreads] = e;
+      }
+      const int2 pt = pb[q];
+      T* own = Fb + pt.x;
+      // the G and f rows read the U parts of this point's C and G rows
+      constexpr int NS = kFactorThreads;
+      if constexpr (sizeof(T) == 4) {
+        check_pivot((double)ilu_row0_32<T, NS>(own, pt.y, Fb, nb), status);
+        asm volatile("" ::: "memory");
+        check_pivot((double)ilu_row1_32<T, NS>(own, pt.y, Fb, nb), status);
+        asm volatile("" ::: "memory");
+        check_pivot((double)ilu_row2_32<T, NS>(own, pt.y, Fb, nb), status);
+      } else {
+        check_pivot((double)ilu_row0_64<T, NS>(own, pt.y, Fb, nb), status);
+        asm volatile("" ::: "memory");
+        check_pivot((double)ilu_row1_64<T, NS>(own, pt.y, Fb, nb), status);
+        asm volatile("" ::: "memory");
+        check_pivot((double)ilu_row2_64<T, NS>(own, pt.y, Fb, nb), status);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// gather, then factor; both on stream s
+template <typename T>
+kkt_status factor_launch(ras_precond* m, cudaStream_t s) {
+  const DevProblem dp = m->prob->dev();
+  long long pmax = 0;
+  for (const BoxDesc& b : m->boxes_h) pmax = std::max(pmax, b.P);
+  const dim3 g((unsigned)((pmax + kGatherThreads - 1) / kGatherThreads), m->nbox);
+  gather_chunks<T><<<g, kGatherThreads, 0, s>>>(dp, m->boxes, m->perm, m->ptab, (T*)m->F);
+  KKT_COUNT(1);
+  KKT_TRY_CUDA(cudaGetLastError());
+  {
+    TimedScope timed(&m->factor_timing, s);
+    ilu0_factor<T><<<m->nbox, kFactorThreads, 0, s>>>(m->boxes, m->iperm, m->perm, m->lptr, m->ptab, (T*)m->F,
+                                                      m->status);
+  }
+  KKT_COUNT(1);
+  KKT_TRY_CUDA(cudaGetLastError());
+  return KKT_OK;
+}
+
+}  // namespace

@@ -1,5 +1,7 @@
 """Generate ilu_rows.inc: straight-line ILU(0) elimination of one KKT row per thread.
 
+(and ilu_slots.inc: the slot list's checksum and each slot's row in a chunk block)
+
 Every row of the space-time KKT matrix is one of three types (C, G, f) with
 a fixed structural stencil of slots (level offset dt, spatial offset, column
 component), ordered as the columns are ordered.  The IKJ elimination of a row
@@ -9,9 +11,15 @@ is therefore the same fixed sequence of operations for every row of a type:
         for each U-slot t of the pivot row k(s) whose column is in the row:
                                      a_s2 <- a_s2 - a_s * u_k[t]
 
-This script writes that sequence out as device code with compile-time slot
-indices, so one thread eliminates one row with the row in registers and the
-pivot-row entries read straight from memory.  The code has no branches: a
+This script writes that elimination out as device code with compile-time slot
+indices, one target entry at a time: entry x of the row receives its updates
+a_x <- a_x - l_s * u_k(s)[t] in increasing L-slot order s (the order IKJ
+applies them), and an L-entry is then scaled by its pivot's reciprocal.  The diagonal slot of a
+finished row holds 1/u_kk rather than u_kk, so a row costs one division
+instead of one per L-slot: a division expands to code with a branch, which
+would stop loads from being issued ahead of it.  Only the multipliers l_s
+stay live in registers; each entry is read, finished and stored in one go, which leaves
+registers for many pivot-row loads in flight.  The code has no branches: a
 pivot point outside the subdomain box is pointed at a stored unit row (1 on
 the diagonals, 0 elsewhere), so its column (which holds 0) contributes
 nothing, and all loads can be issued early.
@@ -20,7 +28,7 @@ The slot order here must equal the one the library builds at run time
 (ras.cu, build_tables); the generated header carries the per-type counts and
 a checksum of the slot list that the library verifies.
 
-    python gen_ilu_rows.py      # rewrites ilu_rows.inc next to this file
+    python gen_ilu_rows.py      # rewrites ilu_slots.inc and ilu_rows.inc next to this file
 """
 
 from __future__ import annotations
@@ -56,11 +64,79 @@ def slot_tables():
     return slots, base, diag, count
 
 
+def slot_rank(s, base, diag, count):
+    """Row of slot s in a chunk block: the L-slots of C, G, f, then the diagonal
+    and U-slots of C, G, f (the order the subdomain solve streams them in)."""
+    nl = [diag[c] - base[c] for c in range(3)]
+    nu = [count[c] - nl[c] for c in range(3)]
+    for c in range(3):
+        if base[c] <= s < diag[c]:
+            return sum(nl[:c]) + (s - base[c])
+    for c in range(3):
+        if diag[c] <= s < base[c] + count[c]:
+            return sum(nl) + sum(nu[:c]) + (s - diag[c])
+    raise ValueError(s)
+
+
 def checksum(slots):
     h = 0
     for i, (dt, dz, dy, dx, cc) in enumerate(slots):
         h = (h * 131 + (i + 1) * (dt + 2) * 7 + (dz + 2) * 11 + (dy + 2) * 13 + (dx + 2) * 17 + cc * 19) % 1000000007
     return h
+
+
+GROUP32 = 8    # entries finished between two rounds of stores, FP32
+GROUP64 = 4    # the same in FP64 (twice the registers per value)
+
+
+def row_function(c, prec, group, nl, cnt, base, slots, diag, rank, nbrs, contrib):
+    """Device code eliminating one row of type c.
+
+    The compiler cannot move a global load above a global store, so the
+    entries are finished in groups of `group`, each group's values stored
+    after all of its loads: a window of loads can be in flight at a time, and
+    the group bounds the registers they take.  The multipliers l_s stay in
+    registers for the rest of the row.
+    """
+    o = [
+        "// own: the point's column in its chunk block (row stride ost); F + nb[i * NS].x: pivot point i's",
+        "// column (the unit row outside the box), nb[i * NS].y: its row stride.  Stores 1/pivot in the",
+        "// diagonal slot and returns the pivot.",
+        "template <typename T, int NS>",
+        f"__device__ __forceinline__ T ilu_row{c}_{prec}(T* __restrict__ own, const int ost, "
+        "const T* __restrict__ F, const int2* __restrict__ nb) {",
+        f"  T l[{nl}], u[{group}], d;",
+    ]
+
+    def accumulate(x, dst):
+        o.append("  {")
+        o.append(f"    T acc = own[{rank[base + x]} * ost];")
+        for (s, i, t) in contrib[x]:
+            o.append(f"    {{ const int2 q = nb[{i} * NS]; acc -= l[{s}] * F[q.x + {rank[t]} * q.y]; }}")
+        if x < nl:
+            dt, dz, dy, dx, ck = slots[base + x]
+            i = nbrs.index((dt, dz, dy, dx))
+            o.append(f"    {{ const int2 q = nb[{i} * NS]; l[{x}] = acc * F[q.x + {rank[diag[ck]]} * q.y]; }}")
+        else:
+            o.append(f"    {dst} = acc;")
+        o.append("  }")
+
+    # groups never straddle the L/U boundary
+    groups = [(g, min(nl, g + group)) for g in range(0, nl, group)]
+    groups += [(g, min(cnt, g + group)) for g in range(nl, cnt, group)]
+    for g0, g1 in groups:
+        for x in range(g0, g1):
+            accumulate(x, f"u[{x - g0}]")
+        if g0 == nl:
+            o.append("  d = u[0];")
+            o.append("  u[0] = (T)1 / u[0];")
+        for x in range(g0, g1):
+            val = f"l[{x}]" if x < nl else f"u[{x - g0}]"
+            o.append(f"  own[{rank[base + x]} * ost] = {val};")
+    o.append("  return d;")
+    o.append("}")
+    o.append("")
+    return o
 
 
 def generate() -> str:
@@ -69,70 +145,78 @@ def generate() -> str:
     for c in range(3):
         for s in range(base[c], base[c] + count[c]):
             index[(c,) + slots[s]] = s
-    out = [
-        "// Generated by gen_ilu_rows.py from the KKT row stencils -- do not edit by hand.",
-        "// Straight-line IKJ ILU(0) elimination of one row of each type (C, G, f).",
-        "#pragma once",
-        "",
-        f"constexpr long long kGenSlotChecksum = {checksum(slots)}LL;",
-        "",
-    ]
-    nbr_tables = []
-    for c in range(3):
-        # distinct pivot points (offsets) of the L-slots, in first-use order
-        nbrs = []
+    # pivot points of all three row types: the f row's list is the union
+    nbrs = []
+    for c in (2, 0, 1):
         for s in range(base[c], diag[c]):
             off = slots[s][:4]
             if off not in nbrs:
                 nbrs.append(off)
-        nbr_tables.append(nbrs)
-        nupd = 0
-        body = []
+    rank = [slot_rank(s, base, diag, count) for s in range(len(slots))]
+    hdr = [
+        "// Generated by gen_ilu_rows.py from the KKT row stencils -- do not edit by hand.",
+        "// Slot list of the three row types (C, G, f) and their rows in a chunk block.",
+        "#pragma once",
+        "",
+        f"constexpr long long kGenSlotChecksum = {checksum(slots)}LL;",
+        f"constexpr int kGenSlots = {len(slots)};",
+        f"constexpr int kGenRowSlots0 = {count[0]}, kGenRowSlots1 = {count[1]}, kGenRowSlots2 = {count[2]};",
+        "// rank of each slot in a chunk block",
+        "constexpr short kGenRank[%d] = {" % len(slots),
+    ]
+    for a in range(0, len(slots), 20):
+        hdr.append("    " + ", ".join(str(r) for r in rank[a:a + 20]) + ",")
+    hdr.append("};")
+    hdr.append("")
+    out = [
+        "// Generated by gen_ilu_rows.py from the KKT row stencils -- do not edit by hand.",
+        "// ILU(0) elimination of one row of each type (C, G, f), one target entry at a time,",
+        "// on the chunk layout (slot s of a point at offset kGenRank[s] * stride).",
+        "#pragma once",
+        "",
+        "// per slot: level offset dt, spatial offsets dz, dy, dx and column component",
+        "__constant__ signed char c_gen_slot[%d][5] = {" % len(slots),
+    ]
+    for a in range(0, len(slots), 8):
+        out.append("    " + ", ".join("{%d, %d, %d, %d, %d}" % sl for sl in slots[a:a + 8]) + ",")
+    out.append("};")
+    out.append("// rank of each slot in a chunk block (device copy of kGenRank)")
+    out.append("__constant__ short c_gen_rank[%d] = {" % len(slots))
+    for a in range(0, len(slots), 20):
+        out.append("    " + ", ".join(str(r) for r in rank[a:a + 20]) + ",")
+    out += [
+        "};",
+        f"constexpr int kGenNbrs = {len(nbrs)};",
+        "// pivot point offsets (dt, dz, dy, dx) shared by the three row types",
+        "__constant__ signed char c_gen_nbr[%d][4] = {" % len(nbrs),
+        "    " + ", ".join(f"{{{dt}, {dz}, {dy}, {dx}}}" for (dt, dz, dy, dx) in nbrs) + "};",
+        "",
+    ]
+    for c in range(3):
+        nl = diag[c] - base[c]
+        # contributions to each target entry x of the row, in increasing L-slot order
+        contrib = {x: [] for x in range(count[c])}
         for s in range(base[c], diag[c]):
             dt, dz, dy, dx, ck = slots[s]
             i = nbrs.index((dt, dz, dy, dx))
-            ls = s - base[c]
-            ups = []
             for t in range(diag[ck] + 1, base[ck] + count[ck]):
                 key = (c, dt + slots[t][0], dz + slots[t][1], dy + slots[t][2], dx + slots[t][3], slots[t][4])
                 if key in index:
-                    ups.append((t, index[key] - base[c]))
-            nupd += len(ups)
-            body.append(f"  {{  // slot {s}: pivot row {'CGf'[ck]} at offset {(dt, dz, dy, dx)}")
-            body.append(f"    const T* u = F + nb[{i} * NS];")
-            body.append(f"    const int st = ns[{i} * NS];")
-            body.append(f"    const T l = a[{ls}] / u[{diag[ck]} * st];")
-            body.append(f"    a[{ls}] = l;")
-            for t, s2 in ups:
-                body.append(f"    a[{s2}] -= l * u[{t} * st];")
-            body.append("  }")
-        out.append(f"// row type {'CGf'[c]}: {count[c]} slots, {diag[c] - base[c]} L-slots, {nupd} updates, "
-                   f"{len(nbrs)} pivot points")
-        out.append(f"constexpr int kGenRowSlots{c} = {count[c]};")
-        out.append(f"constexpr int kGenRowNbrs{c} = {len(nbrs)};")
+                    x = index[key] - base[c]
+                    assert x > s - base[c]
+                    contrib[x].append((s - base[c], i, t))
+        nupd = sum(len(v) for v in contrib.values())
+        out.append(f"// row type {'CGf'[c]}: {count[c]} slots, {nl} L-slots, {nupd} updates")
         out.append(f"constexpr int kGenRowUpdates{c} = {nupd};")
-        out.append("// nb[i * NS]: offset of pivot point i's column in F (the unit row outside the box),")
-        out.append("// ns[i * NS]: row stride of its level block")
-        out.append("template <typename T, int NS>")
-        out.append(f"__device__ __forceinline__ void ilu_elim_row{c}(T* a, const T* __restrict__ F, "
-                   "const int* nb, const int* ns) {")
-        out.extend(body)
-        out.append("}")
-        out.append("")
-    # neighbour offset tables (dt, dz, dy, dx) per row type
-    mx = max(len(n) for n in nbr_tables)
-    out.append(f"constexpr int kGenMaxNbrs = {mx};")
-    out.append("__constant__ signed char c_gen_nbr[3][%d][4] = {" % mx)
-    for c in range(3):
-        rows = [f"{{{dt}, {dz}, {dy}, {dx}}}" for (dt, dz, dy, dx) in nbr_tables[c]]
-        rows += ["{0, 0, 0, 0}"] * (mx - len(rows))
-        out.append("    {" + ", ".join(rows) + "},")
-    out.append("};")
-    return "\n".join(out) + "\n"
+        for prec, gmax in (("32", GROUP32), ("64", GROUP64)):
+            out.extend(row_function(c, prec, gmax, nl, count[c], base[c], slots, diag, rank, nbrs, contrib))
+    return "\n".join(hdr) + "\n", "\n".join(out) + "\n"
 
 
 if __name__ == "__main__":
-    path = os.path.join(HERE, "ilu_rows.inc")
-    with open(path, "w") as fh:
-        fh.write(generate())
-    print(path)
+    slots_h, rows = generate()
+    for name, text in (("ilu_slots.inc", slots_h), ("ilu_rows.inc", rows)):
+        path = os.path.join(HERE, name)
+        with open(path, "w") as fh:
+            fh.write(text)
+        print(path)

@@ -35,8 +35,10 @@
 // ILU(0) (IKJ form, on the structural pattern):
 //   for each row i in order, for each k < i in pattern(i) ascending:
 //     a_ik /= u_kk;  a_ij -= a_ik u_kj  for j > k in pattern(i) and pattern(k).
-// The (row slot, column slot) pairs of the inner update are precomputed per
-// row type as tables of slot indices.
+// The (row slot, column slot) pairs of the inner update are fixed per row
+// type and written out as straight-line code (ilu_rows.inc).  The diagonal
+// slot of a factored row stores 1/u_kk, so both the factorisation and the
+// backward sweep multiply instead of divide.
 //
 // Solve.  One CTA per box runs a two-stage pipeline over its chunks: thread 0
 // issues a TMA bulk copy (cp.async.bulk, completion on an mbarrier) of the
@@ -103,13 +105,17 @@ const SlotTables& tables() {
 
 __constant__ int8_t c_dt[kSlots], c_dz[kSlots], c_dy[kSlots], c_dx[kSlots], c_comp[kSlots];
 __constant__ int c_base[3], c_count[3], c_diag[3];
-__constant__ short c_rank[kSlots];          // slot -> row of the chunk block
-__constant__ short c_slot_of_rank[kSlots];  // row of the chunk block -> slot
+
+// Checksum of the slot list and chunk block rank of every slot, as the
+// generated factorisation code (factor32.cu, factor64.cu) assumes them.
+#include "ilu_slots.inc"
 
 // Slot ranges of the three row types (checked against the tables on the host).
 constexpr int kCBase = 0, kCDiag = 80, kCEnd = 108;
 constexpr int kGBase = 108, kGDiag = 122, kGEnd = 164;
 constexpr int kFBase = 164, kFDiag = 245, kFEnd = 326;
+// span of a box's unit row: kSlots rounded up to whole 16-byte units in FP32 and FP64
+constexpr int kUnitRowSpan = (kSlots + 3) / 4 * 4;
 constexpr int kLRanks = 175;        // L-slots of the three rows
 constexpr int kURanks = 151;        // diagonals and U-slots of the three rows
 
@@ -147,187 +153,6 @@ int chunk_stride(int n) {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-
-template <typename T>
-struct Coefs {
-  const T *S, *ST, *B, *K;
-};
-template <typename T>
-__device__ __forceinline__ Coefs<T> coefs(const DevProblem& p);
-template <>
-__device__ __forceinline__ Coefs<double> coefs<double>(const DevProblem& p) {
-  return {p.S, p.ST, p.B, p.K};
-}
-template <>
-__device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
-  return {p.S32, p.ST32, p.B32, p.K32};
-}
-
-// The factorisation works on a level-major copy of the values: per box and
-// wavefront w a block [slot][point of the wavefront] (row stride = points of
-// the wavefront).  One thread eliminates the rows of one point, and threads
-// of consecutive points read the pivot rows of their neighbours at a common
-// offset from nearly consecutive addresses.  A transpose then writes the
-// chunk blocks the solve streams.
-
-// Fill the slot values of every point of every box from the stencil
-// coefficients: one thread per point, all threads of a warp on the same slot
-// (uniform table reads, and consecutive points of a wavefront write
-// consecutive addresses).  Entries are formed in the factor precision.
-template <typename T>
-__global__ void __launch_bounds__(256) gather_matrix(DevProblem p, const BoxDesc* __restrict__ boxes,
-                                                     const int* __restrict__ perm, const int* __restrict__ lptr,
-                                                     const long long* __restrict__ levoff, T* __restrict__ Flev) {
-  const BoxDesc bx = boxes[blockIdx.y];
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= bx.P) return;
-  T* Fb = Flev + bx.pmoff;
-  const int* lp = lptr + bx.loff;
-  const Coefs<T> cf = coefs<T>(p);
-  const int lex = perm[bx.poff + q];
-  const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-  const int kt = lex / (bx.lx * bx.ly * bx.lz);
-  const int w = kx + 2 * ky + 4 * kz + 8 * kt;
-  const int npts = lp[w + 1] - lp[w];
-  T* dst = Fb + levoff[bx.loff + w] + (q - lp[w]);
-  const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, n = bx.t0 + kt;
-  const int j = gx + p.nx * (gy + p.ny * gz);
-  const bool dirj = p.dir[j] != 0;
-  const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta), b1 = (T)p.beta1, b2 = (T)p.beta2;
-  const T sj = (T)p.sens[j];
-  // time weights of the f row at this level
-  const T mt0 = (n > 0 ? tau / (T)3 : (T)0) + (n < p.M ? tau / (T)3 : (T)0);
-  const T lt0 = (n > 0 ? (T)1 / tau : (T)0) + (n < p.M ? (T)1 / tau : (T)0);
-  const T mt1 = tau / (T)6, lt1 = -(T)1 / tau;
-  for (int s = 0; s < kSlots; ++s) {
-    const int dt = c_dt[s], cc = c_comp[s];
-    const int ax = kx + c_dx[s], ay = ky + c_dy[s], az = kz + c_dz[s], at = kt + dt;
-    T v = 0;
-    if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
-      const int d = (c_dx[s] + 1) + 3 * (c_dy[s] + 1) + 9 * (c_dz[s] + 1);
-      const size_t ci = (size_t)d * p.N + j;
-      if (s < kGBase) {
-        if (n == 0 || dirj) v = (s == kCDiag) ? (T)1 : (T)0;
-        else if (cc == 0) v = dt == 0 ? cf.B[ci] + th * tau * cf.S[ci] : -cf.B[ci] + th1 * tau * cf.S[ci];
-        else v = dt == 0 ? -th * tau * cf.B[ci] : -th1 * tau * cf.B[ci];
-      } else if (s < kFBase) {
-        if (n == p.M || dirj) v = (s == kGDiag) ? (T)1 : (T)0;
-        else if (cc == 1) v = dt == 0 ? cf.B[ci] + th * tau * cf.ST[ci] : -cf.B[ci] + th1 * tau * cf.ST[ci];
-        else v = (dt == 0 ? th1 : th) * tau * sj;
-      } else {
-        const T mt = dt == 0 ? mt0 : mt1, lt = dt == 0 ? lt0 : lt1;
-        v = cc == 1 ? -mt * cf.B[ci] : b1 * lt * cf.B[ci] + b2 * mt * cf.K[ci];
-      }
-    }
-    dst[(long long)s * npts] = v;
-  }
-}
-
-// Chunk blocks [slot rank][cp] of the solve from the level-major factors; one
-// CTA per chunk, staged through shared memory so both sides are contiguous.
-template <typename T>
-__global__ void chunk_transpose(const BoxDesc* __restrict__ boxes, const Chunk* __restrict__ chunks,
-                                const int* __restrict__ lptr, const long long* __restrict__ levoff,
-                                const T* __restrict__ Flev, T* __restrict__ F) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  T* tile = reinterpret_cast<T*>(smem);   // [slot][n]
-  const Chunk c = chunks[blockIdx.x];
-  const BoxDesc bx = boxes[c.box];
-  const int* lp = lptr + bx.loff;
-  const int npts = lp[c.w + 1] - lp[c.w];
-  const T* src = Flev + bx.pmoff + levoff[bx.loff + c.w] + (c.q0 - lp[c.w]);
-  for (int i = threadIdx.x; i < c.n * kSlots; i += blockDim.x) {
-    const int s = i / c.n, jj = i - s * c.n;
-    tile[i] = src[(long long)s * npts + jj];
-  }
-  __syncthreads();
-  T* dst = F + bx.foff + c.off;
-  const int nout = kSlots * c.cp;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    const int r = o / c.cp, jj = o - r * c.cp;
-    dst[o] = jj < c.n ? tile[c_slot_of_rank[r] * c.n + jj] : (T)0;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// ILU(0) factorisation: one CTA per box, one thread per point of a
-// wavefront, rows C, G, f in turn.  The IKJ elimination of a row is the same
-// fixed sequence for every row of a type; ilu_rows.inc holds it as
-// straight-line code (row in registers, compile-time slot indices), and the
-// thread supplies where its pivot points' columns are.
-// ---------------------------------------------------------------------------
-#include "ilu_rows.inc"
-
-constexpr int kFactorThreads = 256;
-
-template <typename T, int C, int NSLOTS, int NNBR>
-__device__ __forceinline__ void factor_row(T* __restrict__ Fb, const int* __restrict__ iperm_b,
-                                           const int* __restrict__ lp, const long long* __restrict__ lo,
-                                           const BoxDesc& bx, int w, int own, int ost, int kx, int ky, int kz,
-                                           int kt, int unit_row, int* nb, int* ns, int* __restrict__ status) {
-  constexpr int base = C == 0 ? kCBase : (C == 1 ? kGBase : kFBase);
-  constexpr int diag = C == 0 ? kCDiag : (C == 1 ? kGDiag : kFDiag);
-  // where the pivot points' columns are (offset in Fb and row stride)
-#pragma unroll 1
-  for (int i = 0; i < NNBR; ++i) {
-    const int dt = c_gen_nbr[C][i][0], dz = c_gen_nbr[C][i][1], dy = c_gen_nbr[C][i][2], dx = c_gen_nbr[C][i][3];
-    const int ax = kx + dx, ay = ky + dy, az = kz + dz, at = kt + dt;
-    int off = unit_row, st = 1;
-    if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
-      const int qk = iperm_b[ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))];
-      const int wk = w + dx + 2 * dy + 4 * dz + 8 * dt;
-      off = (int)lo[wk] + (qk - lp[wk]);
-      st = lp[wk + 1] - lp[wk];
-    }
-    nb[i * kFactorThreads] = off;
-    ns[i * kFactorThreads] = st;
-  }
-  T a[NSLOTS];
-#pragma unroll
-  for (int i = 0; i < NSLOTS; ++i) a[i] = Fb[own + (long long)(base + i) * ost];
-  if (C == 0) ilu_elim_row0<T, kFactorThreads>(a, Fb, nb, ns);
-  if (C == 1) ilu_elim_row1<T, kFactorThreads>(a, Fb, nb, ns);
-  if (C == 2) ilu_elim_row2<T, kFactorThreads>(a, Fb, nb, ns);
-#pragma unroll
-  for (int i = 0; i < NSLOTS; ++i) Fb[own + (long long)(base + i) * ost] = a[i];
-  const double d = (double)a[diag - base];
-  if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* __restrict__ boxes,
-                                                                 const int* __restrict__ perm,
-                                                                 const int* __restrict__ iperm,
-                                                                 const int* __restrict__ lptr,
-                                                                 const long long* __restrict__ levoff,
-                                                                 T* __restrict__ Flev, int* __restrict__ status) {
-  __shared__ int nbs[kGenMaxNbrs * kFactorThreads], nss[kGenMaxNbrs * kFactorThreads];
-  const BoxDesc bx = boxes[blockIdx.x];
-  T* Fb = Flev + bx.pmoff;
-  const int* lp = lptr + bx.loff;
-  const long long* lo = levoff + bx.loff;
-  const int* ip = iperm + bx.poff;
-  int* nb = nbs + threadIdx.x;
-  int* ns = nss + threadIdx.x;
-  const int unit_row = (int)lo[bx.nlev];
-  // the unit row: 1 at the three diagonal slots, 0 elsewhere
-  for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
-    Fb[unit_row + s] = (s == kCDiag || s == kGDiag || s == kFDiag) ? (T)1 : (T)0;
-  __syncthreads();
-  for (int w = 0; w < bx.nlev; ++w) {
-    const int npts = lp[w + 1] - lp[w];
-    for (int j = threadIdx.x; j < npts; j += blockDim.x) {
-      const int lex = perm[bx.poff + lp[w] + j];
-      const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-      const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      const int own = (int)lo[w] + j;
-      factor_row<T, 0, kGenRowSlots0, kGenRowNbrs0>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, unit_row, nb, ns, status);
-      factor_row<T, 1, kGenRowSlots1, kGenRowNbrs1>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, unit_row, nb, ns, status);
-      factor_row<T, 2, kGenRowSlots2, kGenRowNbrs2>(Fb, ip, lp, lo, bx, w, own, npts, kx, ky, kz, kt, unit_row, nb, ns, status);
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // TMA bulk copies and mbarriers (inline PTX)
@@ -504,7 +329,7 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
     const T* B = b ? buf1 : buf0;
     const bool act = j < c.n;
     T* vp = v;
-    T v0 = 0, v1 = 0, v2 = 0, d0 = 1, d1 = 1, d2 = 1;
+    T v0 = 0, v1 = 0, v2 = 0, r0 = 1, r1 = 1, r2 = 1;   // r: reciprocals of the pivots
     if (act) {
       const int lex = perm[bx.poff + c.q0 + j];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
@@ -513,9 +338,9 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
       v0 = vp[0];
       v1 = vp[1];
       v2 = vp[2];
-      d0 = B[0 * c.cp + j];
-      d1 = B[28 * c.cp + j];
-      d2 = B[70 * c.cp + j];
+      r0 = B[0 * c.cp + j];
+      r1 = B[28 * c.cp + j];
+      r2 = B[70 * c.cp + j];
     }
     // Every U-slot reads a point of a later wavefront except the C row's
     // own-f slot (U block row 1), applied after the f row is solved.
@@ -523,9 +348,9 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
     const T bG = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
     const T bC = row_dot<2, 28, 80>(B, c.cp, j, off, vp, lane, act);
     if (act && lane == 0) {
-      const T zf = (v2 - bF) / d2;
-      const T zg = (v1 - bG) / d1;
-      const T zc = (v0 - bC - B[1 * c.cp + j] * zf) / d0;
+      const T zf = (v2 - bF) * r2;
+      const T zg = (v1 - bG) * r1;
+      const T zc = (v0 - bC - B[1 * c.cp + j] * zf) * r0;
       vp[0] = zc;
       vp[1] = zg;
       vp[2] = zf;
@@ -595,6 +420,11 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       set_error("ras_setup: generated elimination code does not match the slot tables");
       return KKT_ERR_ARG;
     }
+    for (int i = 0; i < kSlots; ++i)
+      if (kGenRank[i] != slot_rank(i)) {
+        set_error("ras_setup: generated elimination code does not match the chunk block order");
+        return KKT_ERR_ARG;
+      }
   }
   if (T.base[0] != kCBase || T.diag[0] != kCDiag || T.base[1] != kGBase || T.diag[1] != kGDiag ||
       T.base[2] != kFBase || T.diag[2] != kFDiag || T.base[2] + T.count[2] != kFEnd) {
@@ -603,9 +433,6 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   }
   static bool consts_done = false;   // constant memory is per module; upload once per process
   if (!consts_done) {
-    short rank[kSlots], inv[kSlots];
-    for (int s = 0; s < kSlots; ++s) rank[s] = (short)slot_rank(s);
-    for (int s = 0; s < kSlots; ++s) inv[rank[s]] = (short)s;
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dt, T.dt, kSlots));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dz, T.dz, kSlots));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dy, T.dy, kSlots));
@@ -614,8 +441,6 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_base, T.base, sizeof(T.base)));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_count, T.count, sizeof(T.count)));
     KKT_TRY_CUDA(cudaMemcpyToSymbol(c_diag, T.diag, sizeof(T.diag)));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_rank, rank, sizeof(rank)));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_slot_of_rank, inv, sizeof(inv)));
     consts_done = true;
   }
 
@@ -629,9 +454,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   std::vector<BoxDesc> boxes;
   std::vector<int> perm, iperm, lptr;
-  std::vector<long long> levoff;
+  std::vector<int2> ptab;
   std::vector<Chunk> chunks;
-  long long foff = 0, voff = 0, pmoff = 0;
+  long long foff = 0, voff = 0;
   for (int it = 0; it < nsub[3]; ++it)
     for (int iz = 0; iz < nsub[2]; ++iz)
       for (int iy = 0; iy < nsub[1]; ++iy)
@@ -650,8 +475,6 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           b.P = (long long)b.lx * b.ly * b.lz * b.lt;
           b.nlev = (b.lx - 1) + 2 * (b.ly - 1) + 4 * (b.lz - 1) + 8 * (b.lt - 1) + 1;
           b.foff = foff;
-          b.pmoff = pmoff;
-          pmoff += b.P * kSlots + kSlots;     // + the unit row of pivot points outside the box
           b.voff = voff;
           b.poff = (long long)perm.size();
           b.loff = (long long)lptr.size();
@@ -664,13 +487,6 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
                 for (int kx = 0; kx < b.lx; ++kx) cnt[kx + 2 * ky + 4 * kz + 8 * kt + 1]++;
           for (int w = 0; w < b.nlev; ++w) cnt[w + 1] += cnt[w];
           for (int w = 0; w <= b.nlev; ++w) lptr.push_back(cnt[w]);
-          {
-            long long acc = 0;
-            for (int w = 0; w <= b.nlev; ++w) {
-              levoff.push_back(acc);
-              if (w < b.nlev) acc += (long long)kSlots * (cnt[w + 1] - cnt[w]);
-            }
-          }
           std::vector<int> bp(b.P), bi(b.P);
           std::vector<int> fill(cnt.begin(), cnt.end() - 1);
           int lex = 0;
@@ -686,6 +502,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           iperm.insert(iperm.end(), bi.begin(), bi.end());
           // chunks of each wavefront and the storage offset of every point
           b.cbeg = (int)chunks.size();
+          const size_t pt0 = ptab.size();
+          ptab.resize(pt0 + b.P);
           long long off = 0;
           for (int w = 0; w < b.nlev; ++w)
             for (int q0 = cnt[w]; q0 < cnt[w + 1]; q0 += CH) {
@@ -696,10 +514,20 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
               c.n = std::min(CH, cnt[w + 1] - q0);
               c.cp = stride(c.n);
               c.off = off;
+              for (int k = 0; k < c.n; ++k) ptab[pt0 + q0 + k] = make_int2((int)(off + k), c.cp);
               off += (long long)kSlots * c.cp;
               chunks.push_back(c);
             }
           b.cend = (int)chunks.size();
+          // the unit row of pivot points outside the box, padded so that the
+          // next box's blocks start on a 16-byte boundary (bulk copies need it)
+          b.unit = off;
+          off += kUnitRowSpan;
+          if (off > INT32_MAX) {
+            set_error("ras_setup: a subdomain holds more than 2^31 factor values; use more subdomains");
+            delete m;
+            return KKT_ERR_ARG;
+          }
           foff += off;
           boxes.push_back(b);
         }
@@ -712,6 +540,18 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   for (const BoxDesc& b : boxes)
     m->max_pad = std::max(m->max_pad, 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2));
   const size_t esz = factor_prec == 64 ? sizeof(double) : sizeof(float);
+  // every bulk copy of the solve must start on a 16-byte boundary and move a
+  // multiple of 16 bytes: check each chunk's L and U blocks before any launch
+  for (const Chunk& c : chunks) {
+    const long long base = (boxes[c.box].foff + c.off) * (long long)esz;
+    const long long lbytes = (long long)kLRanks * c.cp * (long long)esz;
+    const long long ubytes = (long long)kURanks * c.cp * (long long)esz;
+    if (base % 16 || lbytes % 16 || ubytes % 16) {
+      set_error("ras_setup: internal error: a factor block is not 16-byte aligned");
+      delete m;
+      return KKT_ERR_ARG;
+    }
+  }
   auto fail = [&](kkt_status st, const char* what) {
     cudaGetLastError();
     set_error(std::string("ras_setup: ") + what);
@@ -722,8 +562,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->perm, perm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->iperm, iperm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->lptr, lptr.size() * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&m->Fpm, pmoff * esz) != cudaSuccess ||
-      cudaMalloc(&m->levoff, levoff.size() * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&m->ptab, ptab.size() * sizeof(int2)) != cudaSuccess ||
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
       cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * esz) != cudaSuccess ||
       cudaMalloc(&m->status, sizeof(int)) != cudaSuccess)
@@ -733,8 +572,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (e == cudaSuccess) e = cudaMemcpy(m->perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->lptr, lptr.data(), lptr.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->levoff, levoff.data(), levoff.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->ptab, ptab.data(), ptab.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * esz);
@@ -750,22 +588,6 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
 }
 
 namespace {
-
-template <typename T>
-kkt_status launch_factor(ras_precond* m, cudaStream_t s) {
-  {
-    TimedScope timed(&m->factor_timing, s);
-    ilu0_factor<T><<<m->nbox, kFactorThreads, 0, s>>>(m->boxes, m->perm, m->iperm, m->lptr, m->levoff, (T*)m->Fpm,
-                                                      m->status);
-  }
-  const size_t tsmem = (size_t)ChunkCfg<T>::CH * kSlots * sizeof(T);
-  KKT_TRY_CUDA(cudaFuncSetAttribute(chunk_transpose<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
-  chunk_transpose<T><<<m->nchunk, 256, tsmem, s>>>(m->boxes, m->chunks, m->lptr, m->levoff, (const T*)m->Fpm,
-                                                   (T*)m->F);
-  KKT_COUNT(2);
-  KKT_TRY_CUDA(cudaGetLastError());
-  return KKT_OK;
-}
 
 template <typename T>
 kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaStream_t s) {
@@ -790,20 +612,9 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaSt
 }  // namespace
 
 kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
-  const DevProblem dp = m->prob->dev();
-  long long pmax = 0;
-  for (const BoxDesc& b : m->boxes_h) pmax = std::max(pmax, b.P);
-  dim3 g((unsigned)((pmax + 255) / 256), m->nbox);
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
-  if (m->prec == 64) {
-    gather_matrix<double><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->lptr, m->levoff, (double*)m->Fpm);
-    KKT_COUNT(1);
-    KKT_TRY(launch_factor<double>(m, s));
-  } else {
-    gather_matrix<float><<<g, 256, 0, s>>>(dp, m->boxes, m->perm, m->lptr, m->levoff, (float*)m->Fpm);
-    KKT_COUNT(1);
-    KKT_TRY(launch_factor<float>(m, s));
-  }
+  if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
+  else KKT_TRY(ras_factor_launch32(m, s));
   int st = 0;
   KKT_TRY_CUDA(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   KKT_TRY_CUDA(cudaStreamSynchronize(s));
@@ -897,8 +708,7 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->perm);
   cudaFree(m->iperm);
   cudaFree(m->lptr);
-  cudaFree(m->Fpm);
-  cudaFree(m->levoff);
+  cudaFree(m->ptab);
   cudaFree(m->chunks);
   cudaFree(m->F);
   cudaFree(m->V);

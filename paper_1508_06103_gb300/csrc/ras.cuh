@@ -26,7 +26,7 @@ struct BoxDesc {
   int nlev;                    // wavefronts x + 2y + 4z + 8t
   long long P;                 // points of the extended box
   long long foff;              // offset of the box's chunk blocks (elements)
-  long long pmoff;             // offset of the box's level-major factor values (elements)
+  long long unit;              // offset of the box's unit row within its factor values (elements)
   long long voff;              // offset of the box's padded local vector (elements)
   long long poff;              // offset into perm / iperm
   long long loff;              // offset into the wavefront pointers
@@ -47,8 +47,8 @@ struct ras_precond {
   int* lptr = nullptr;         // wavefront pointers per box (nlev + 1 each)
   Chunk* chunks = nullptr;
   int nchunk = 0;
-  void* Fpm = nullptr;         // level-major factor values (factorisation)
-  long long* levoff = nullptr; // per box and wavefront: offset of its block in Fpm
+  int2* ptab = nullptr;        // per point (wavefront order): {offset of its column in the box's
+                               // chunk blocks, row stride of its block}
   void* F = nullptr;           // factor values
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;
@@ -59,5 +59,8 @@ struct ras_precond {
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
                       ras_precond** out);
 kkt_status ras_factor(ras_precond* m, cudaStream_t s);
+// gather and ILU(0) launches of factor32.cu / factor64.cu
+kkt_status ras_factor_launch32(ras_precond* m, cudaStream_t s);
+kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s);
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s);
 kkt_status ras_check(ras_precond* m);
