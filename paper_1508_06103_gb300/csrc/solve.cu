@@ -43,7 +43,10 @@ struct Grid4 {
 
 // fine y = I^h_c yc (multilinear in x, y, z, t); one thread per fine point.
 // Per axis the fine index i = I r + rem takes (1 - rem/r) of coarse I and
-// rem/r of coarse I + 1 (the second weight is 0 on coarse points).
+// rem/r of coarse I + 1 (the second weight is 0 on coarse points).  A is the
+// arithmetic type: FP64, or FP32 inside the mixed-precision preconditioner
+// (vectors stay FP64 in memory).
+template <typename A>
 __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ yc,
                               double* __restrict__ y) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -52,27 +55,27 @@ __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, 
   const int j = (int)(idx - (long long)n * f.N);
   const int ix = j % f.nx, iy = (j / f.nx) % f.ny, iz = j / (f.nx * f.ny);
   const int X0 = ix / rx, Y0 = iy / ry, Z0 = iz / rz, T0 = n / rt;
-  const double wx = (double)(ix - X0 * rx) / rx, wy = (double)(iy - Y0 * ry) / ry;
-  const double wz = (double)(iz - Z0 * rz) / rz, wt = (double)(n - T0 * rt) / rt;
+  const A wx = (A)(ix - X0 * rx) / (A)rx, wy = (A)(iy - Y0 * ry) / (A)ry;
+  const A wz = (A)(iz - Z0 * rz) / (A)rz, wt = (A)(n - T0 * rt) / (A)rt;
   const int X1 = wx > 0 ? X0 + 1 : X0, Y1 = wy > 0 ? Y0 + 1 : Y0, Z1 = wz > 0 ? Z0 + 1 : Z0, T1 = wt > 0 ? T0 + 1 : T0;
   const int xs[2] = {X0, X1}, ys[2] = {Y0, Y1}, zs[2] = {Z0, Z1}, ts[2] = {T0, T1};
-  const double wxs[2] = {1.0 - wx, wx}, wys[2] = {1.0 - wy, wy}, wzs[2] = {1.0 - wz, wz}, wts[2] = {1.0 - wt, wt};
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  const A wxs[2] = {(A)1 - wx, wx}, wys[2] = {(A)1 - wy, wy}, wzs[2] = {(A)1 - wz, wz}, wts[2] = {(A)1 - wt, wt};
+  A a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
   for (int at = 0; at < 2; ++at)
 #pragma unroll
     for (int az = 0; az < 2; ++az)
 #pragma unroll
       for (int ay = 0; ay < 2; ++ay) {
-        const double w3 = wts[at] * wzs[az] * wys[ay];
+        const A w3 = wts[at] * wzs[az] * wys[ay];
         const double* src = yc + 3 * ((long long)ts[at] * c.N + c.nx * (ys[ay] + c.ny * zs[az]));
 #pragma unroll
         for (int ax = 0; ax < 2; ++ax) {
-          const double w = w3 * wxs[ax];
+          const A w = w3 * wxs[ax];
           const double* q = src + 3 * xs[ax];
-          a0 += w * q[0];
-          a1 += w * q[1];
-          a2 += w * q[2];
+          a0 += w * (A)q[0];
+          a1 += w * (A)q[1];
+          a2 += w * (A)q[2];
         }
       }
   y[3 * idx] = a0;
@@ -81,7 +84,9 @@ __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, 
 }
 
 // coarse rc = (I^h_c)^T x; one thread per coarse point gathers its fine
-// support: fine index I r + a, |a| < r, weight 1 - |a|/r per axis.
+// support: fine index I r + a, |a| < r, weight 1 - |a|/r per axis.  A as in
+// interp_kernel.
+template <typename A>
 __global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ x,
                                 double* __restrict__ rc) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -93,21 +98,21 @@ __global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt
   const int y0 = max(J * ry - ry + 1, 0), y1 = min(J * ry + ry - 1, f.ny - 1);
   const int z0 = max(K * rz - rz + 1, 0), z1 = min(K * rz + rz - 1, f.nz - 1);
   const int t0 = max(n * rt - rt + 1, 0), t1 = min(n * rt + rt - 1, f.L - 1);
-  const double irx = 1.0 / rx, iry = 1.0 / ry, irz = 1.0 / rz, irt = 1.0 / rt;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  const A irx = (A)1 / (A)rx, iry = (A)1 / (A)ry, irz = (A)1 / (A)rz, irt = (A)1 / (A)rt;
+  A a0 = 0, a1 = 0, a2 = 0;
   for (int ft = t0; ft <= t1; ++ft) {
-    const double wt = 1.0 - abs(ft - n * rt) * irt;
+    const A wt = (A)1 - (A)abs(ft - n * rt) * irt;
     for (int fz = z0; fz <= z1; ++fz) {
-      const double wz = wt * (1.0 - abs(fz - K * rz) * irz);
+      const A wz = wt * ((A)1 - (A)abs(fz - K * rz) * irz);
       for (int fy = y0; fy <= y1; ++fy) {
-        const double wy = wz * (1.0 - abs(fy - J * ry) * iry);
+        const A wy = wz * ((A)1 - (A)abs(fy - J * ry) * iry);
         const double* row = x + 3 * ((long long)ft * f.N + f.nx * (fy + f.ny * fz));
         for (int fx = x0; fx <= x1; ++fx) {
-          const double w = wy * (1.0 - abs(fx - I * rx) * irx);
+          const A w = wy * ((A)1 - (A)abs(fx - I * rx) * irx);
           const double* q = row + 3 * fx;
-          a0 += w * q[0];
-          a1 += w * q[1];
-          a2 += w * q[2];
+          a0 += w * (A)q[0];
+          a1 += w * (A)q[1];
+          a2 += w * (A)q[2];
         }
       }
     }
@@ -152,7 +157,9 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   kkt_problem* pf = c->fine;
   kkt_problem* pc = c->cp;
   const Grid4 gf = grid_of(pf), gc = grid_of(pc);
-  restrict_kernel<<<(unsigned)((pc->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
+  const unsigned rblocks = (unsigned)((pc->P + 255) / 256), iblocks = (unsigned)((pf->P + 255) / 256);
+  if (c->prec == 64) restrict_kernel<double><<<rblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
+  else restrict_kernel<float><<<rblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   CoarseOp Ac(pc, c->prec, c->cx32, c->cy32);
@@ -161,7 +168,8 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   KKT_TRY(gmres_run(Ac, &Mc, c->rc, c->yc, c->ws, c->c_maxit, c->c_rtol, c->c_maxit, false, true, &r, s));
   if (r.status < 0) return r.status;
   c->last_coarse_iters = r.iters;
-  interp_kernel<<<(unsigned)((pf->P + 255) / 256), 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
+  if (c->prec == 64) interp_kernel<double><<<iblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
+  else interp_kernel<float><<<iblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   if (c->prec == 64) KKT_TRY(launch_residual(pf->dev(), x, c->y, c->t, s));   // t = x - F_h y
@@ -230,7 +238,10 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
   kkt_status st = create_problem(&cg, cnt, fine->tau * c->rt, ac.data(), vc.data(), sc.empty() ? nullptr : sc.data(),
                                  (int)sc.size(), fine->beta1, fine->beta2, fine->theta, &c->cp);
   if (st == KKT_OK) st = ras_create(c->cp, nsub_c, c_overlap, 0, factor_prec, &c->cras);
-  if (st == KKT_OK) st = c->ws.alloc(c->cp->n, c_maxit, false);
+  // The coarse GMRES keeps z_j = M_c^{-1} v_j (the flexible form's store, c_maxit
+  // coarse vectors) and forms y_c = Z y: for its fixed preconditioner this is
+  // the right-preconditioned iterate M_c^{-1} V y with one application less.
+  if (st == KKT_OK) st = c->ws.alloc(c->cp->n, c_maxit, true);
   if (st == KKT_OK &&
       (cudaMalloc(&c->rc, c->cp->n * sizeof(double)) != cudaSuccess ||
        cudaMalloc(&c->yc, c->cp->n * sizeof(double)) != cudaSuccess ||
