@@ -452,8 +452,9 @@ def kernel_arm(args):
         torch.cuda.synchronize()
         info = ras.info()
         ms = e0.elapsed_time(e1) / args.reps
-        by = info["factor_values"] * info["value_bytes"] + info["points"] * 24 + prob.n * 8
-        out.update(info, ms=ms, alg_bytes=by, gbs=by / ms / 1e6)
+        # algorithmic bytes: unpadded factor values, gathered residual, owned output
+        by = info["points"] * SLOTS_PER_POINT * info["value_bytes"] + info["points"] * 24 + prob.n * 8
+        out.update(info, shape=ras.solve_shape(), ms=ms, alg_bytes=by, gbs=by / ms / 1e6)
     else:
         xs, ys = x.float(), torch.empty(prob.n, dtype=torch.float32, device="cuda")
         for name, (a, b_) in (("fp64", (x, y)), ("fp32", (xs, ys))):

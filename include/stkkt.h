@@ -147,6 +147,15 @@ kkt_status ras_info(const ras_precond* m, int* nbox, long long* points, long lon
                     int* value_bytes);
 
 /*
+ * ras_solve_shape -- how the subdomain solve of a preconditioner runs (chosen
+ *   at ras_setup from the boxes' sizes and the device's occupancy): points per
+ *   chunk of a wavefront, buffers of its factor-copy ring, and 1 if the local
+ *   vectors live in shared memory.  Any output may be NULL.  Reporting only;
+ *   the paper has no counterpart.
+ */
+kkt_status ras_solve_shape(const ras_precond* m, int* chunk_points, int* stages, int* smem_vectors);
+
+/*
  * ras_apply -- z = sum_ij (R^0_ij)^T M_ij^{-1} R^delta_ij r (restricted prolongation,
  *   Cai-Sarkis form cited in Sec. 3.2); all boxes in one launch.  r, z FP64, must
  *   not overlap.

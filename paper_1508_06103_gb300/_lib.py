@@ -47,6 +47,7 @@ SIGNATURES = {
     "ras_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ras_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                            C.POINTER(C.c_int)]),
+    "ras_solve_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "coarse_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
     "kkt_launch_count": (C.c_longlong, []),
     "kkt_timing_enable": (C.c_int, [C.c_int]),

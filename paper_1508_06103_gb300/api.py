@@ -134,6 +134,12 @@ class RAS:
         check(self._lib.ras_info(self.h, C.byref(nb), C.byref(pts), C.byref(fv), C.byref(vb)), "ras_info")
         return dict(nbox=nb.value, points=pts.value, factor_values=fv.value, value_bytes=vb.value)
 
+    def solve_shape(self):
+        """dict(chunk_points, stages, smem_vectors) of the subdomain solve."""
+        ch, ns, sv = C.c_int(), C.c_int(), C.c_int()
+        check(self._lib.ras_solve_shape(self.h, C.byref(ch), C.byref(ns), C.byref(sv)), "ras_solve_shape")
+        return dict(chunk_points=ch.value, stages=ns.value, smem_vectors=bool(sv.value))
+
     def timing(self, kernel: int = 0):
         """(total ms, launches) since the last reset: kernel 0 subdomain solve, 1 factorisation."""
         ms, n = C.c_double(), C.c_longlong()

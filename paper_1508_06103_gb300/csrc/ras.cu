@@ -55,6 +55,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -134,14 +135,14 @@ struct ChunkCfg;
 template <>
 struct ChunkCfg<float> {
   static constexpr int CH = 56;       // points per chunk (4 lanes each: 7 full warps)
+  static constexpr int CH2 = 40, CH3 = 24;   // smaller chunks (row strides 40, 24) for small boxes
   static constexpr int Q = 16, R = 8; // row stride cp = 8 (mod 16): conflict-free 4-lane reads
-  static constexpr int CHP = 56;      // largest row stride (that of a full chunk)
 };
 template <>
 struct ChunkCfg<double> {
   static constexpr int CH = 32;       // 4 full warps
+  static constexpr int CH2 = 20, CH3 = 12;   // smaller chunks (row strides 20, 12)
   static constexpr int Q = 8, R = 4;  // cp = 4 (mod 8)
-  static constexpr int CHP = 36;
 };
 
 template <typename T>
@@ -205,8 +206,9 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned pari
 // With SMEM the box's padded local vector lives in shared memory as well.
 // ---------------------------------------------------------------------------
 constexpr int kLanes = 4;
-constexpr size_t kSmemLimit = 227 * 1024;
-constexpr int kSolveHeader = 2048;   // off[] table and the two mbarriers
+constexpr size_t kSmemLimit = 227 * 1024;          // dynamic shared memory of one CTA
+constexpr int kSolveHeader = 2048;   // off[] table (326 ints) and, from byte 1536, the mbarriers
+constexpr int kMaxStages = 4;        // buffers of the subdomain solve's copy ring
 
 // sum over block rows [R0, R1) of B[r*cp + j] * vp[off[r + SOFF]]
 template <int R0, int R1, int SOFF, typename T>
@@ -227,45 +229,52 @@ template <typename T, bool SMEM>
 __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
     const BoxDesc* __restrict__ boxes, const int* __restrict__ perm, const Chunk* __restrict__ chunks,
     const T* __restrict__ F, T* __restrict__ V, const double* __restrict__ r, double* __restrict__ z, int nx, int ny,
-    int N, int* __restrict__ status) {
+    int N, int bstride, int nstage, int* __restrict__ status) {
   static_assert((ChunkCfg<T>::CH * kLanes) % 32 == 0, "the solve needs full warps");
   extern __shared__ __align__(128) unsigned char smem[];
   int* off = reinterpret_cast<int*>(smem);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
-  T* buf0 = reinterpret_cast<T*>(smem + kSolveHeader);
-  T* buf1 = buf0 + (size_t)kLRanks * ChunkCfg<T>::CHP;
+  T* buf0 = reinterpret_cast<T*>(smem + kSolveHeader);   // nstage buffers of bstride values
+                                                        // (kLRanks x the largest chunk row stride)
   const BoxDesc bx = boxes[blockIdx.x];
   const long long P = bx.P;
   const T* Fb = F + bx.foff;
   const int px = bx.lx + 2, py = bx.ly + 2, pz = bx.lz + 2;
   const long long sy = px, sz = (long long)px * py, st = (long long)px * py * pz;
   const long long npad = 3 * st * (bx.lt + 2);
-  T* v = SMEM ? buf1 + (size_t)kLRanks * ChunkCfg<T>::CHP : V + bx.voff;
+  T* v = SMEM ? buf0 + (size_t)nstage * bstride : V + bx.voff;
   const int nch = bx.cend - bx.cbeg;
   const Chunk* ck = chunks + bx.cbeg;
   for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
     off[s] = (int)(3 * (c_dx[s] + sy * c_dy[s] + sz * c_dz[s] + st * c_dt[s]) + c_comp[s]);
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < nstage; ++b) mbar_init(&bar[b], 1);
     mbar_fence_init();
   }
   if (SMEM)
     for (long long i = threadIdx.x; i < npad; i += blockDim.x) v[i] = (T)0;
   __syncthreads();
-  // stream the L block of chunk 0 while the right-hand side is gathered
-  unsigned phase = 0;   // bit b = parity of the next completion of bar[b]
-  auto issue = [&](int i, bool upper, int b) {
-    const Chunk c = ck[i];
+  // The factor blocks stream in the order L(0), ..., L(nch-1), U(nch-1), ...,
+  // U(0) through a ring of `nstage` buffers: block g goes to buffer g mod
+  // nstage and is copied nstage - 1 steps before it is used.
+  const int nblk = 2 * nch;
+  auto chunk_of = [&](int g) { return g < nch ? g : nblk - 1 - g; };
+  auto issue = [&](const Chunk& c, int g) {
+    const bool upper = g >= nch;
+    const int b = g % nstage;
     const unsigned rows = upper ? kURanks : kLRanks;
     const unsigned bytes = rows * (unsigned)c.cp * (unsigned)sizeof(T);
     const T* src = Fb + c.off + (upper ? (long long)kLRanks * c.cp : 0);
     fence_proxy_async();
     mbar_expect_tx(&bar[b], bytes);
-    bulk_g2s(b ? buf1 : buf0, src, bytes, &bar[b]);
+    bulk_g2s(buf0 + (size_t)b * bstride, src, bytes, &bar[b]);
   };
-  if (threadIdx.x == 0 && nch > 0) issue(0, false, 0);
-  // gather R^delta r into the padded local vector
+  Chunk iss;   // thread 0: descriptor of the next block to copy
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < min(nstage - 1, nblk); ++g) issue(ck[chunk_of(g)], g);
+    if (nstage - 1 < nblk) iss = ck[chunk_of(nstage - 1)];
+  }
+  // gather R^delta r into the padded local vector while the first blocks arrive
   for (long long q = threadIdx.x; q < P; q += blockDim.x) {
     const int kx = (int)(q % bx.lx), ky = (int)((q / bx.lx) % bx.ly), kz = (int)((q / (bx.lx * bx.ly)) % bx.lz);
     const int kt = (int)(q / ((long long)bx.lx * bx.ly * bx.lz));
@@ -278,84 +287,95 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
   }
   __syncthreads();
   const int lane = threadIdx.x & (kLanes - 1), j = threadIdx.x / kLanes;
-  // forward sweep with the unit lower factor
-  for (int i = 0; i < nch; ++i) {
-    const int b = i & 1;
-    if (threadIdx.x == 0) {
-      if (i + 1 < nch) issue(i + 1, false, b ^ 1);
-      else issue(nch - 1, true, b ^ 1);          // first U block of the backward sweep
+  // padded-vector offset of this thread's point from its lexicographic index
+  auto point_offset = [&](int lex) -> long long {
+    const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
+    const int kt = lex / (bx.lx * bx.ly * bx.lz);
+    return 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
+  };
+  // Step g works on the chunk of block g (`cur`).  The descriptor of the
+  // chunk after next and the point index of the next chunk are loaded one
+  // step ahead, so the only loads left between a barrier and the arithmetic
+  // are the vector's.  Steps 0..nch-1 are the forward sweep with the unit
+  // lower factor, steps nch..2 nch-1 the backward sweep with the upper factor.
+  Chunk cur, nxt;
+  int lex_cur = 0;
+  if (nblk > 0) {
+    cur = ck[0];
+    nxt = ck[chunk_of(min(1, nblk - 1))];
+    lex_cur = j < cur.n ? perm[bx.poff + cur.q0 + j] : 0;
+  }
+  // one step of either sweep
+  auto step = [&](int g, auto upper_tag) {
+    constexpr bool kUpper = decltype(upper_tag)::value;
+    const int b = g % nstage;
+    if (threadIdx.x == 0 && g + nstage - 1 < nblk) {
+      issue(iss, g + nstage - 1);
+      if (g + nstage < nblk) iss = ck[chunk_of(g + nstage)];
     }
-    mbar_wait(&bar[b], (phase >> b) & 1u, status);
-    phase ^= 1u << b;
-    const Chunk c = ck[i];
-    const T* B = b ? buf1 : buf0;
+    const Chunk nn = ck[chunk_of(min(g + 2, nblk - 1))];
+    const int lex_nxt = (g + 1 < nblk && j < nxt.n) ? perm[bx.poff + nxt.q0 + j] : 0;
+    mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status);
+    const Chunk& c = cur;
+    const T* B = buf0 + (size_t)b * bstride;
     const bool act = j < c.n;
     T* vp = v;
     T v0 = 0, v1 = 0, v2 = 0;
     if (act) {
-      const int lex = perm[bx.poff + c.q0 + j];
-      const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-      const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      vp = v + 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
+      vp = v + point_offset(lex_cur);
       v0 = vp[0];
       v1 = vp[1];
       v2 = vp[2];
     }
-    // Every L-slot reads a point of an earlier wavefront except the G row's
-    // own-C slot (block row 93) and the f row's own-G slot (row 174), so the
-    // three rows' sums over other points are gathered together and the two
-    // own-point terms are applied afterwards in C, G, f order.
-    const T aC = row_dot<0, 80, 0>(B, c.cp, j, off, vp, lane, act);
-    const T aG = row_dot<80, 93, 28>(B, c.cp, j, off, vp, lane, act);
-    const T aF = row_dot<94, 174, 70>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) {
-      const T yc = v0 - aC;
-      const T yg = v1 - aG - B[93 * c.cp + j] * yc;
-      const T yf = v2 - aF - B[174 * c.cp + j] * yg;
-      vp[0] = yc;
-      vp[1] = yg;
-      vp[2] = yf;
+    if constexpr (!kUpper) {
+      // Every L-slot reads a point of an earlier wavefront except the G row's
+      // own-C slot (block row 93) and the f row's own-G slot (row 174), so the
+      // three rows' sums over other points are gathered together and the two
+      // own-point terms are applied afterwards in C, G, f order.
+      const T aC = row_dot<0, 80, 0>(B, c.cp, j, off, vp, lane, act);
+      const T aG = row_dot<80, 93, 28>(B, c.cp, j, off, vp, lane, act);
+      const T aF = row_dot<94, 174, 70>(B, c.cp, j, off, vp, lane, act);
+      if (act && lane == 0) {
+        const T yc = v0 - aC;
+        const T yg = v1 - aG - B[93 * c.cp + j] * yc;
+        const T yf = v2 - aF - B[174 * c.cp + j] * yg;
+        vp[0] = yc;
+        vp[1] = yg;
+        vp[2] = yf;
+      }
+    } else {
+      // Every U-slot reads a point of a later wavefront except the C row's
+      // own-f slot (U block row 1), applied after the f row is solved.  The
+      // diagonal rows 0, 28, 70 hold the reciprocals of the pivots.
+      const T bF = row_dot<71, 151, 175>(B, c.cp, j, off, vp, lane, act);
+      const T bG = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
+      const T bC = row_dot<2, 28, 80>(B, c.cp, j, off, vp, lane, act);
+      if (act && lane == 0) {
+        const T zf = (v2 - bF) * B[70 * c.cp + j];
+        const T zg = (v1 - bG) * B[28 * c.cp + j];
+        const T zc = (v0 - bC - B[1 * c.cp + j] * zf) * B[0 * c.cp + j];
+        vp[0] = zc;
+        vp[1] = zg;
+        vp[2] = zf;
+      }
     }
     __syncthreads();
-  }
-  // backward sweep with the upper factor
-  for (int k = 0; k < nch; ++k) {
-    const int i = nch - 1 - k;
-    const int b = (nch + k) & 1;
-    if (threadIdx.x == 0 && k + 1 < nch) issue(i - 1, true, b ^ 1);
-    mbar_wait(&bar[b], (phase >> b) & 1u, status);
-    phase ^= 1u << b;
-    const Chunk c = ck[i];
-    const T* B = b ? buf1 : buf0;
-    const bool act = j < c.n;
-    T* vp = v;
-    T v0 = 0, v1 = 0, v2 = 0, r0 = 1, r1 = 1, r2 = 1;   // r: reciprocals of the pivots
-    if (act) {
-      const int lex = perm[bx.poff + c.q0 + j];
-      const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-      const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      vp = v + 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
-      v0 = vp[0];
-      v1 = vp[1];
-      v2 = vp[2];
-      r0 = B[0 * c.cp + j];
-      r1 = B[28 * c.cp + j];
-      r2 = B[70 * c.cp + j];
+    cur = nxt;
+    nxt = nn;
+    lex_cur = lex_nxt;
+  };
+  // Forward sweep (unit lower factor), then backward sweep (upper factor).
+  // FP64 runs them as two loops, FP32 as one loop with the direction decided
+  // per step: the faster form of each as measured at 32^3 x 64 (FP64 12.2 ms
+  // vs 28 ms with one loop; FP32 3.7 ms vs 4.2 ms with two).
+  if constexpr (sizeof(T) == 4) {
+    for (int g = 0; g < nblk; ++g) {
+      if (g < nch) step(g, std::false_type{});
+      else step(g, std::true_type{});
     }
-    // Every U-slot reads a point of a later wavefront except the C row's
-    // own-f slot (U block row 1), applied after the f row is solved.
-    const T bF = row_dot<71, 151, 175>(B, c.cp, j, off, vp, lane, act);
-    const T bG = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
-    const T bC = row_dot<2, 28, 80>(B, c.cp, j, off, vp, lane, act);
-    if (act && lane == 0) {
-      const T zf = (v2 - bF) * r2;
-      const T zg = (v1 - bG) * r1;
-      const T zc = (v0 - bC - B[1 * c.cp + j] * zf) * r0;
-      vp[0] = zc;
-      vp[1] = zg;
-      vp[2] = zf;
-    }
-    __syncthreads();
+  } else {
+    for (int g = 0; g < nch; ++g) step(g, std::false_type{});
+    for (int g = nch; g < nblk; ++g) step(g, std::true_type{});
   }
   // scatter the owned part: (R^0)^T
   const int ox = bx.ox1 - bx.ox0, oy = bx.oy1 - bx.oy0, oz = bx.oz1 - bx.oz0, ot = bx.ot1 - bx.ot0;
@@ -384,10 +404,53 @@ std::vector<std::pair<int, int>> parts(int n, int p) {
   return out;
 }
 
+size_t solve_smem(int cpmax, int nstage, size_t esz, long long max_pad, bool smem_vec) {
+  const size_t bufs = (size_t)nstage * kLRanks * cpmax * esz;
+  return kSolveHeader + bufs + (smem_vec ? (size_t)max_pad * esz : 0);
+}
+
+// Chunk size, copy-ring depth and local-vector placement of the subdomain
+// solve.  Each box is one CTA that steps through its chunks one after the
+// other, so a step's latency decides the time, and most of it is the gathers
+// of neighbour values from the local vector.  The order of preference, as
+// measured on GB300 at 32^3 x 64 (fine boxes) and 16^3 x 32 (coarse-sized
+// boxes), FP32 and FP64: the local vector in shared memory when it fits; the
+// fewest waves of CTAs over the SMs (the runtime's occupancy for the shared
+// memory, threads and registers); the shallowest ring (a deeper ring takes
+// shared memory from the L1 that caches a global local vector, and lost
+// 30-45 % in every case measured); the largest chunk (fewest steps).
+struct SolveShape {
+  int ch, cpmax, nstage;
+  bool smem_vec;
+};
 template <typename T>
-size_t solve_smem(long long max_pad, bool smem_vec) {
-  const size_t bufs = 2 * (size_t)kLRanks * ChunkCfg<T>::CHP * sizeof(T);
-  return kSolveHeader + bufs + (smem_vec ? (size_t)max_pad * sizeof(T) : 0);
+kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, SolveShape* out) {
+  const int cands[3] = {ChunkCfg<T>::CH, ChunkCfg<T>::CH2, ChunkCfg<T>::CH3};
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+  SolveShape best{ChunkCfg<T>::CH, chunk_stride<T>(ChunkCfg<T>::CH), 2, false};
+  long long best_key = -1;
+  for (int ci = 0; ci < 3; ++ci)
+    for (int ns = 2; ns <= kMaxStages; ++ns)
+      for (int sv = 1; sv >= 0; --sv) {
+        const int ch = cands[ci], cp = chunk_stride<T>(ch);
+        const size_t sm = solve_smem(cp, ns, sizeof(T), max_pad, sv != 0);
+        if (sm > kSmemLimit) continue;
+        const int threads = (ch * kLanes + 31) / 32 * 32;
+        int per_sm = 0;
+        KKT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, sv ? (const void*)ras_solve<T, true> : (const void*)ras_solve<T, false>, threads, sm));
+        if (per_sm < 1) continue;
+        const long long waves = (nbox + (long long)nsm * per_sm - 1) / ((long long)nsm * per_sm);
+        // smaller key is better
+        const long long key = (sv ? 0 : 1000000000LL) + waves * 100000 + (ns - 2) * 1000 + (100 - ch);
+        if (best_key < 0 || key < best_key) {
+          best_key = key;
+          best = SolveShape{ch, cp, ns, sv != 0};
+        }
+      }
+  *out = best;
+  return KKT_OK;
 }
 
 }  // namespace
@@ -448,10 +511,40 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (!m) return KKT_ERR_NOMEM;
   m->prob = p;
   m->prec = factor_prec;
-  const int CH = factor_prec == 64 ? ChunkCfg<double>::CH : ChunkCfg<float>::CH;
   auto stride = [&](int n) { return factor_prec == 64 ? chunk_stride<double>(n) : chunk_stride<float>(n); };
   std::vector<std::pair<int, int>> pr[4];
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
+  {
+    // largest padded local vector: boxes are products of one part per axis
+    long long pad = 3;
+    for (int a = 0; a < 4; ++a) {
+      int mx = 0;
+      for (const auto& q : pr[a])
+        mx = std::max(mx, std::min(dims[a], q.second + overlap) - std::max(0, q.first - overlap));
+      pad *= mx + 2;
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+      cudaGetLastError();
+      set_error("ras_setup: cannot query the current device");
+      delete m;
+      return KKT_ERR_CUDA;
+    }
+    const int nbox = nsub[0] * nsub[1] * nsub[2] * nsub[3];
+    SolveShape sh{};
+    const kkt_status cs = factor_prec == 64 ? choose_solve_shape<double>(nbox, pad, nsm, &sh)
+                                            : choose_solve_shape<float>(nbox, pad, nsm, &sh);
+    if (cs != KKT_OK) {
+      delete m;
+      return cs;
+    }
+    m->ch = sh.ch;
+    m->cpmax = sh.cpmax;
+    m->smem_vec = sh.smem_vec;
+    m->nstage = sh.nstage;
+  }
+  const int CH = m->ch;
   std::vector<BoxDesc> boxes;
   std::vector<int> perm, iperm, lptr;
   std::vector<int2> ptab;
@@ -592,17 +685,17 @@ namespace {
 template <typename T>
 kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaStream_t s) {
   const kkt_problem* p = m->prob;
-  const int threads = ChunkCfg<T>::CH * kLanes;
-  const size_t with_vec = solve_smem<T>(m->max_pad, true);
-  if (with_vec <= kSmemLimit) {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)with_vec));
-    ras_solve<T, true><<<m->nbox, threads, with_vec, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r,
-                                                          z, p->nx, p->ny, p->N, m->status);
+  const int threads = (m->ch * kLanes + 31) / 32 * 32;
+  const int bstride = kLRanks * m->cpmax;
+  const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(T), m->max_pad, m->smem_vec);
+  if (m->smem_vec) {
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ras_solve<T, true><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r, z,
+                                                      p->nx, p->ny, p->N, bstride, m->nstage, m->status);
   } else {
-    const size_t smem = solve_smem<T>(m->max_pad, false);
     KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ras_solve<T, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r, z,
-                                                       p->nx, p->ny, p->N, m->status);
+                                                       p->nx, p->ny, p->N, bstride, m->nstage, m->status);
   }
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
@@ -656,6 +749,17 @@ extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void
     return KKT_ERR_ARG;
   }
   return ras_launch(m, r, z, (cudaStream_t)stream);
+}
+
+extern "C" kkt_status ras_solve_shape(const ras_precond* m, int* chunk_points, int* stages, int* smem_vectors) {
+  if (!m) {
+    set_error("ras_solve_shape: null argument");
+    return KKT_ERR_ARG;
+  }
+  if (chunk_points) *chunk_points = m->ch;
+  if (stages) *stages = m->nstage;
+  if (smem_vectors) *smem_vectors = m->smem_vec ? 1 : 0;
+  return KKT_OK;
 }
 
 extern "C" kkt_status ras_info(const ras_precond* m, int* nbox, long long* points, long long* factor_values,

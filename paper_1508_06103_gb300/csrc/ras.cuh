@@ -37,6 +37,10 @@ struct ras_precond {
   kkt_problem* prob = nullptr;
   int prec = 64;               // factor / solve precision (64 or 32)
   int nbox = 0;
+  int ch = 0;                  // points per chunk of the subdomain solve (chosen per preconditioner)
+  int cpmax = 0;               // largest chunk row stride
+  bool smem_vec = false;       // solve keeps the local vectors in shared memory
+  int nstage = 2;              // buffers of the solve's copy ring
   long long fcount = 0;        // factor values
   long long max_pad = 0;       // largest padded local vector (elements)
   long long vcount = 0;        // elements of all padded local vectors (the solve's scratch)
