@@ -336,6 +336,14 @@ def gpu_arm(args):
     fp64 = dict(last)
     del ras64, co64
 
+    # ---- mixed form with BF16-stored factors (FP32 factorisation and sweeps) --
+    torch.cuda.synchronize()
+    ras16, co16 = make(16)
+    step(ras16, co16, cobs)
+    bf16_ms = timed(lambda: step(ras16, co16, cobs), args.fp64_steps)
+    bf16 = dict(last)
+    del ras16, co16
+
     # ---- the KKT matvec on its own (FP64 and FP32) --------------------------
     xm = torch.randn(prob.n, dtype=torch.float64, device="cuda")
     ym = torch.empty_like(xm)
@@ -384,6 +392,8 @@ def gpu_arm(args):
         "fp64_form": {"s_per_solve": fp64_ms / 1e3, "iterations": fp64.get("iters"),
                       "true_relres": fp64.get("relres"), "steps": args.fp64_steps},
         "mixed_speedup_vs_fp64": fp64_ms / ms,
+        "bf16_factor_form": {"s_per_solve": bf16_ms / 1e3, "iterations": bf16.get("iters"),
+                             "true_relres": bf16.get("relres"), "steps": args.fp64_steps},
         "matvec": {"fp64_gbs": mv64_bytes / (mv64_ms * 1e-3) / 1e9, "fp64_us": mv64_ms * 1e3,
                    "fp32_gbs": mv32_bytes / (mv32_ms * 1e-3) / 1e9, "fp32_us": mv32_ms * 1e3,
                    "fp64_frac": mv64_bytes / (mv64_ms * 1e-3) / 1e9 / peak,

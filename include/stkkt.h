@@ -131,7 +131,9 @@ kkt_status kkt_residual(kkt_problem* p, const double* b, const double* x, double
  *   (homogeneous Dirichlet conditions on all cut space and time faces,
  *   Eq. 10-12) and is factored by ILU(0) on its structural pattern.
  *   local        0 = ILU(0) (the only local solver of this version).
- *   factor_prec  64 = factor and solve in FP64, 32 = FP32.
+ *   factor_prec  64 = factor and solve in FP64, 32 = FP32, 16 = factor in FP32
+ *                and store the factors as BF16 (round to nearest); the solve
+ *                converts them to FP32 and accumulates in FP32.
  *   All boxes factor in one launch, synchronously; errors: ARG, NOMEM, CUDA,
  *   ZERO_PIVOT.
  */

@@ -160,19 +160,19 @@ __global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* 
   }
 }
 
-// gather, then factor; both on stream s
+// gather, then factor, in place on F (chunk layout); both on stream s
 template <typename T>
-kkt_status factor_launch(ras_precond* m, cudaStream_t s) {
+kkt_status factor_launch(ras_precond* m, T* F, cudaStream_t s) {
   const DevProblem dp = m->prob->dev();
   long long pmax = 0;
   for (const BoxDesc& b : m->boxes_h) pmax = std::max(pmax, b.P);
   const dim3 g((unsigned)((pmax + kGatherThreads - 1) / kGatherThreads), m->nbox);
-  gather_chunks<T><<<g, kGatherThreads, 0, s>>>(dp, m->boxes, m->perm, m->ptab, (T*)m->F);
+  gather_chunks<T><<<g, kGatherThreads, 0, s>>>(dp, m->boxes, m->perm, m->ptab, F);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   {
     TimedScope timed(&m->factor_timing, s);
-    ilu0_factor<T><<<m->nbox, kFactorThreads, 0, s>>>(m->boxes, m->iperm, m->perm, m->lptr, m->ptab, (T*)m->F,
+    ilu0_factor<T><<<m->nbox, kFactorThreads, 0, s>>>(m->boxes, m->iperm, m->perm, m->lptr, m->ptab, F,
                                                       m->status);
   }
   KKT_COUNT(1);

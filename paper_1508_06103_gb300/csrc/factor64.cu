@@ -3,4 +3,4 @@
 
 #include "factor.cuh"
 
-kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s) { return factor_launch<double>(m, s); }
+kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s) { return factor_launch<double>(m, (double*)m->F, s); }

@@ -58,6 +58,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 #include "ras.cuh"
 
@@ -145,6 +147,31 @@ struct ChunkCfg<double> {
   static constexpr int Q = 8, R = 4;  // cp = 4 (mod 8)
 };
 
+template <>
+struct ChunkCfg<__nv_bfloat16> {     // FP32 factors stored as BF16
+  static constexpr int CH = 80;       // 10 full warps
+  static constexpr int CH2 = 48, CH3 = 16;
+  static constexpr int Q = 32, R = 16; // cp = 16 (mod 32): two values per bank word, conflict-free
+};
+
+// arithmetic type of the solve for a storage type (BF16 factors: FP32)
+template <typename S>
+struct SolveArith {
+  using type = S;
+};
+template <>
+struct SolveArith<__nv_bfloat16> {
+  using type = float;
+};
+template <typename T, typename S>
+__device__ __forceinline__ T arith(S v) {
+  return static_cast<T>(v);
+}
+template <>
+__device__ __forceinline__ float arith<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
 template <typename T>
 int chunk_stride(int n) {
   const int Q = ChunkCfg<T>::Q, R = ChunkCfg<T>::R;
@@ -211,38 +238,40 @@ constexpr int kSolveHeader = 2048;   // off[] table (326 ints) and, from byte 15
 constexpr int kMaxStages = 4;        // buffers of the subdomain solve's copy ring
 
 // sum over block rows [R0, R1) of B[r*cp + j] * vp[off[r + SOFF]]
-template <int R0, int R1, int SOFF, typename T>
-__device__ __forceinline__ T row_dot(const T* __restrict__ B, int cp, int j, const int* __restrict__ off,
+template <int R0, int R1, int SOFF, typename S, typename T>
+__device__ __forceinline__ T row_dot(const S* __restrict__ B, int cp, int j, const int* __restrict__ off,
                                      const T* vp, int lane, bool act) {
   T acc = 0;
 #pragma unroll
   for (int k = 0; k < (R1 - R0 + kLanes - 1) / kLanes; ++k) {
     const int r = R0 + lane + k * kLanes;
-    if (act && r < R1) acc += B[r * cp + j] * vp[off[r + SOFF]];
+    if (act && r < R1) acc += arith<T>(B[r * cp + j]) * vp[off[r + SOFF]];
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   return acc;
 }
 
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
+// S: type of the stored factor values; T: arithmetic and local-vector type
+template <typename S, bool SMEM>
+__global__ void __launch_bounds__(ChunkCfg<S>::CH * kLanes) ras_solve(
     const BoxDesc* __restrict__ boxes, const int* __restrict__ perm, const Chunk* __restrict__ chunks,
-    const T* __restrict__ F, T* __restrict__ V, const double* __restrict__ r, double* __restrict__ z, int nx, int ny,
-    int N, int bstride, int nstage, int* __restrict__ status) {
-  static_assert((ChunkCfg<T>::CH * kLanes) % 32 == 0, "the solve needs full warps");
+    const S* __restrict__ F, typename SolveArith<S>::type* __restrict__ V, const double* __restrict__ r,
+    double* __restrict__ z, int nx, int ny, int N, int bstride, int nstage, int* __restrict__ status) {
+  using T = typename SolveArith<S>::type;
+  static_assert((ChunkCfg<S>::CH * kLanes) % 32 == 0, "the solve needs full warps");
   extern __shared__ __align__(128) unsigned char smem[];
   int* off = reinterpret_cast<int*>(smem);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
-  T* buf0 = reinterpret_cast<T*>(smem + kSolveHeader);   // nstage buffers of bstride values
+  S* buf0 = reinterpret_cast<S*>(smem + kSolveHeader);   // nstage buffers of bstride values
                                                         // (kLRanks x the largest chunk row stride)
   const BoxDesc bx = boxes[blockIdx.x];
   const long long P = bx.P;
-  const T* Fb = F + bx.foff;
+  const S* Fb = F + bx.foff;
   const int px = bx.lx + 2, py = bx.ly + 2, pz = bx.lz + 2;
   const long long sy = px, sz = (long long)px * py, st = (long long)px * py * pz;
   const long long npad = 3 * st * (bx.lt + 2);
-  T* v = SMEM ? buf0 + (size_t)nstage * bstride : V + bx.voff;
+  T* v = SMEM ? reinterpret_cast<T*>(buf0 + (size_t)nstage * bstride) : V + bx.voff;
   const int nch = bx.cend - bx.cbeg;
   const Chunk* ck = chunks + bx.cbeg;
   for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
@@ -263,8 +292,8 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
     const bool upper = g >= nch;
     const int b = g % nstage;
     const unsigned rows = upper ? kURanks : kLRanks;
-    const unsigned bytes = rows * (unsigned)c.cp * (unsigned)sizeof(T);
-    const T* src = Fb + c.off + (upper ? (long long)kLRanks * c.cp : 0);
+    const unsigned bytes = rows * (unsigned)c.cp * (unsigned)sizeof(S);
+    const S* src = Fb + c.off + (upper ? (long long)kLRanks * c.cp : 0);
     fence_proxy_async();
     mbar_expect_tx(&bar[b], bytes);
     bulk_g2s(buf0 + (size_t)b * bstride, src, bytes, &bar[b]);
@@ -317,7 +346,7 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
     const int lex_nxt = (g + 1 < nblk && j < nxt.n) ? perm[bx.poff + nxt.q0 + j] : 0;
     mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status);
     const Chunk& c = cur;
-    const T* B = buf0 + (size_t)b * bstride;
+    const S* B = buf0 + (size_t)b * bstride;
     const bool act = j < c.n;
     T* vp = v;
     T v0 = 0, v1 = 0, v2 = 0;
@@ -337,8 +366,8 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
       const T aF = row_dot<94, 174, 70>(B, c.cp, j, off, vp, lane, act);
       if (act && lane == 0) {
         const T yc = v0 - aC;
-        const T yg = v1 - aG - B[93 * c.cp + j] * yc;
-        const T yf = v2 - aF - B[174 * c.cp + j] * yg;
+        const T yg = v1 - aG - arith<T>(B[93 * c.cp + j]) * yc;
+        const T yf = v2 - aF - arith<T>(B[174 * c.cp + j]) * yg;
         vp[0] = yc;
         vp[1] = yg;
         vp[2] = yf;
@@ -351,9 +380,9 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
       const T bG = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
       const T bC = row_dot<2, 28, 80>(B, c.cp, j, off, vp, lane, act);
       if (act && lane == 0) {
-        const T zf = (v2 - bF) * B[70 * c.cp + j];
-        const T zg = (v1 - bG) * B[28 * c.cp + j];
-        const T zc = (v0 - bC - B[1 * c.cp + j] * zf) * B[0 * c.cp + j];
+        const T zf = (v2 - bF) * arith<T>(B[70 * c.cp + j]);
+        const T zg = (v1 - bG) * arith<T>(B[28 * c.cp + j]);
+        const T zc = (v0 - bC - arith<T>(B[1 * c.cp + j]) * zf) * arith<T>(B[0 * c.cp + j]);
         vp[0] = zc;
         vp[1] = zg;
         vp[2] = zf;
@@ -368,7 +397,7 @@ __global__ void __launch_bounds__(ChunkCfg<T>::CH * kLanes) ras_solve(
   // FP64 runs them as two loops, FP32 as one loop with the direction decided
   // per step: the faster form of each as measured at 32^3 x 64 (FP64 12.2 ms
   // vs 28 ms with one loop; FP32 3.7 ms vs 4.2 ms with two).
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {   // FP32 and BF16-stored factors
     for (int g = 0; g < nblk; ++g) {
       if (g < nch) step(g, std::false_type{});
       else step(g, std::true_type{});
@@ -404,9 +433,10 @@ std::vector<std::pair<int, int>> parts(int n, int p) {
   return out;
 }
 
-size_t solve_smem(int cpmax, int nstage, size_t esz, long long max_pad, bool smem_vec) {
+// esz: bytes of a stored factor value, vsz: of a local-vector value
+size_t solve_smem(int cpmax, int nstage, size_t esz, size_t vsz, long long max_pad, bool smem_vec) {
   const size_t bufs = (size_t)nstage * kLRanks * cpmax * esz;
-  return kSolveHeader + bufs + (smem_vec ? (size_t)max_pad * esz : 0);
+  return kSolveHeader + bufs + (smem_vec ? (size_t)max_pad * vsz : 0);
 }
 
 // Chunk size, copy-ring depth and local-vector placement of the subdomain
@@ -434,7 +464,7 @@ kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, SolveShape* 
     for (int ns = 2; ns <= kMaxStages; ++ns)
       for (int sv = 1; sv >= 0; --sv) {
         const int ch = cands[ci], cp = chunk_stride<T>(ch);
-        const size_t sm = solve_smem(cp, ns, sizeof(T), max_pad, sv != 0);
+        const size_t sm = solve_smem(cp, ns, sizeof(T), sizeof(typename SolveArith<T>::type), max_pad, sv != 0);
         if (sm > kSmemLimit) continue;
         const int threads = (ch * kLanes + 31) / 32 * 32;
         int per_sm = 0;
@@ -468,8 +498,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       set_error("ras_setup: each nsub must lie in [1, points along that axis]");
       return KKT_ERR_ARG;
     }
-  if (overlap < 0 || local != 0 || (factor_prec != 64 && factor_prec != 32)) {
-    set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)), factor_prec 64 or 32");
+  if (overlap < 0 || local != 0 || (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
+    set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)), factor_prec 64, 32 or 16");
     return KKT_ERR_ARG;
   }
   const SlotTables& T = tables();
@@ -511,7 +541,10 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (!m) return KKT_ERR_NOMEM;
   m->prob = p;
   m->prec = factor_prec;
-  auto stride = [&](int n) { return factor_prec == 64 ? chunk_stride<double>(n) : chunk_stride<float>(n); };
+  auto stride = [&](int n) {
+    return factor_prec == 64 ? chunk_stride<double>(n)
+                             : (factor_prec == 32 ? chunk_stride<float>(n) : chunk_stride<__nv_bfloat16>(n));
+  };
   std::vector<std::pair<int, int>> pr[4];
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   {
@@ -533,8 +566,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     }
     const int nbox = nsub[0] * nsub[1] * nsub[2] * nsub[3];
     SolveShape sh{};
-    const kkt_status cs = factor_prec == 64 ? choose_solve_shape<double>(nbox, pad, nsm, &sh)
-                                            : choose_solve_shape<float>(nbox, pad, nsm, &sh);
+    const kkt_status cs = factor_prec == 64   ? choose_solve_shape<double>(nbox, pad, nsm, &sh)
+                          : factor_prec == 32 ? choose_solve_shape<float>(nbox, pad, nsm, &sh)
+                                              : choose_solve_shape<__nv_bfloat16>(nbox, pad, nsm, &sh);
     if (cs != KKT_OK) {
       delete m;
       return cs;
@@ -632,7 +666,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   m->max_pad = 0;
   for (const BoxDesc& b : boxes)
     m->max_pad = std::max(m->max_pad, 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2));
-  const size_t esz = factor_prec == 64 ? sizeof(double) : sizeof(float);
+  // bytes of a stored factor value and of a local-vector value
+  const size_t esz = factor_prec == 64 ? sizeof(double) : (factor_prec == 32 ? sizeof(float) : 2);
+  const size_t vsz = factor_prec == 64 ? sizeof(double) : sizeof(float);
   // every bulk copy of the solve must start on a 16-byte boundary and move a
   // multiple of 16 bytes: check each chunk's L and U blocks before any launch
   for (const Chunk& c : chunks) {
@@ -657,7 +693,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->lptr, lptr.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->ptab, ptab.size() * sizeof(int2)) != cudaSuccess ||
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
-      cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * esz) != cudaSuccess ||
+      cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * vsz) != cudaSuccess ||
+      (factor_prec == 16 && cudaMalloc(&m->Ffac, foff * sizeof(float)) != cudaSuccess) ||
       cudaMalloc(&m->status, sizeof(int)) != cudaSuccess)
     return fail(KKT_ERR_NOMEM, "device allocation failed");
   cudaError_t e = cudaSuccess;
@@ -668,7 +705,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (e == cudaSuccess) e = cudaMemcpy(m->ptab, ptab.data(), ptab.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
-  if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * esz);
+  if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * vsz);
+  if (e == cudaSuccess && m->Ffac) e = cudaMemset(m->Ffac, 0, foff * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
   if (e != cudaSuccess) return fail(KKT_ERR_CUDA, cudaGetErrorString(e));
   kkt_status st = ras_factor(m, nullptr);
@@ -682,19 +720,21 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
 
 namespace {
 
-template <typename T>
-kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaStream_t s) {
+template <typename S>
+kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
+                        cudaStream_t s) {
+  using T = typename SolveArith<S>::type;
   const kkt_problem* p = m->prob;
   const int threads = (m->ch * kLanes + 31) / 32 * 32;
   const int bstride = kLRanks * m->cpmax;
-  const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(T), m->max_pad, m->smem_vec);
+  const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(S), sizeof(T), m->max_pad, m->smem_vec);
   if (m->smem_vec) {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<T, true><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r, z,
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ras_solve<S, true><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
                                                       p->nx, p->ny, p->N, bstride, m->nstage, m->status);
   } else {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<T, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const T*)m->F, V, r, z,
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ras_solve<S, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
                                                        p->nx, p->ny, p->N, bstride, m->nstage, m->status);
   }
   KKT_COUNT(1);
@@ -707,7 +747,8 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, T* V, cudaSt
 kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
   if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
-  else KKT_TRY(ras_factor_launch32(m, s));
+  else if (m->prec == 32) KKT_TRY(ras_factor_launch32(m, s));
+  else KKT_TRY(ras_factor_launch16(m, s));
   int st = 0;
   KKT_TRY_CUDA(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   KKT_TRY_CUDA(cudaStreamSynchronize(s));
@@ -721,7 +762,8 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s) {
   TimedScope timed(&m->timing, s);
   if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s);
-  return launch_solve<float>(m, r, z, (float*)m->V, s);
+  if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s);
+  return launch_solve<__nv_bfloat16>(m, r, z, (float*)m->V, s);
 }
 
 kkt_status ras_check(ras_precond* m) {
@@ -773,7 +815,7 @@ extern "C" kkt_status ras_info(const ras_precond* m, int* nbox, long long* point
   if (nbox) *nbox = m->nbox;
   if (points) *points = pts;
   if (factor_values) *factor_values = m->fcount;
-  if (value_bytes) *value_bytes = m->prec == 64 ? 8 : 4;
+  if (value_bytes) *value_bytes = m->prec == 64 ? 8 : (m->prec == 32 ? 4 : 2);
   return KKT_OK;
 }
 
@@ -813,6 +855,7 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->iperm);
   cudaFree(m->lptr);
   cudaFree(m->ptab);
+  cudaFree(m->Ffac);
   cudaFree(m->chunks);
   cudaFree(m->F);
   cudaFree(m->V);
@@ -880,5 +923,6 @@ extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* 
   // any handle) may have left other data at those positions
   KKT_TRY_CUDA(cudaMemsetAsync(scratch, 0, bytes, s));
   if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)scratch, s);
-  return launch_solve<float>(m, r, z, (float*)scratch, s);
+  if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)scratch, s);
+  return launch_solve<__nv_bfloat16>(m, r, z, (float*)scratch, s);
 }

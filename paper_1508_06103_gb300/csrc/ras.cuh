@@ -35,7 +35,7 @@ struct BoxDesc {
 
 struct ras_precond {
   kkt_problem* prob = nullptr;
-  int prec = 64;               // factor / solve precision (64 or 32)
+  int prec = 64;               // factor storage: 64, 32, or 16 (BF16; factorisation and solve in FP32)
   int nbox = 0;
   int ch = 0;                  // points per chunk of the subdomain solve (chosen per preconditioner)
   int cpmax = 0;               // largest chunk row stride
@@ -53,7 +53,8 @@ struct ras_precond {
   int nchunk = 0;
   int2* ptab = nullptr;        // per point (wavefront order): {offset of its column in the box's
                                // chunk blocks, row stride of its block}
-  void* F = nullptr;           // factor values
+  void* F = nullptr;           // factor values (FP64, FP32 or BF16, as the solve reads them)
+  void* Ffac = nullptr;        // BF16 storage: the FP32 values the factorisation works on
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;
   TimingLog timing;            // subdomain-solve launches
@@ -66,5 +67,6 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s);
 // gather and ILU(0) launches of factor32.cu / factor64.cu
 kkt_status ras_factor_launch32(ras_precond* m, cudaStream_t s);
 kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s);
+kkt_status ras_factor_launch16(ras_precond* m, cudaStream_t s);   // FP32 factorisation, BF16 store
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s);
 kkt_status ras_check(ras_precond* m);

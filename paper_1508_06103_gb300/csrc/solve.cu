@@ -210,7 +210,7 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
   c->rt = fine->M / cnt;
   c->c_rtol = c_rtol;
   c->c_maxit = c_maxit;
-  c->prec = factor_prec == 32 ? 32 : 64;
+  c->prec = factor_prec == 64 ? 64 : 32;   // FP32 arithmetic with FP32 or BF16-stored factors
   // coarse coefficients: cell means of the fine cells
   const int ncc = ccx * ccy * ccz;
   std::vector<double> ac(ncc, 0.0), vc(3 * (size_t)ncc, 0.0);

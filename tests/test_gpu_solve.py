@@ -12,8 +12,11 @@ Tolerances:
   against the oracle's sparse direct solve, after solving to rtol 1e-13 (the
   KKT matrix is ill-conditioned, so a 1e-8 residual alone does not give a
   1e-8 error).
-* mixed solve (FP32 factors, FP64 Krylov): recovered source f within 1e-5
-  relative L2 of the oracle's direct solve, after solving to rtol 1e-10.
+* mixed solve (FP32 or BF16-stored factors, FP64 Krylov): recovered source f
+  within 1e-5 relative L2 of the oracle's direct solve, after solving to
+  rtol 1e-10.
+* one-level RAS, BF16-stored factors: relative 2-norm difference to the
+  oracle's FP64 ILU(0) apply <= 8 u_bf16 (u = 2^-8).
 """
 
 import numpy as np
@@ -78,6 +81,24 @@ def test_ras_apply_fp32_close_to_oracle(api):
     assert np.linalg.norm(z - zr) <= 1e-3 * np.linalg.norm(zr)
 
 
+def test_ras_apply_bf16_close_to_oracle(api):
+    # BF16 keeps 8 significant bits (unit roundoff u = 2^-8 = 3.9e-3); the
+    # factors are rounded once after an FP32 factorisation and the sweeps
+    # accumulate in FP32, so the preconditioned vector moves by a few u
+    case = RAS_CASES[0]
+    w = W.random_small(nsens=6, **case["w"])
+    p = okkt.Problem.from_workload(w)
+    ref = osch.RAS(p, okkt.assemble(p), case["nsub"], case["ov"], "ilu0")
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, case["nsub"], case["ov"], 16)
+    assert ras.info()["value_bytes"] == 2
+    for seed in (3, 4):
+        r = W.random_vector(prob.n, seed)
+        zr = ref.apply(r)
+        z = ras.apply(_dev(r)).cpu().numpy()
+        assert np.linalg.norm(z - zr) <= 8 * 2.0**-8 * np.linalg.norm(zr)
+
+
 def _two_level_case():
     return W.mid(cells=(4, 4, 4), M=8, nsub=(2, 2, 2, 2), overlap=1, coarse_cells=(2, 2, 2), coarse_M=4)
 
@@ -119,7 +140,7 @@ def test_one_level_fp64_solve_matches_direct_solve(api):
     assert np.linalg.norm(b - F @ xe) <= 1e-12 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 16])
 def test_two_level_solve_matches_direct_solve(api, prec):
     w = W.mid(cells=(6, 6, 6), M=6, nsub=(2, 2, 2, 2), overlap=1, coarse_cells=(3, 3, 3), coarse_M=3)
     p, F, cobs, b, U = _exact(w)
