@@ -130,7 +130,12 @@ kkt_status kkt_residual(kkt_problem* p, const double* b, const double* x, double
  *   subdomain matrix is the principal submatrix of F_h on the extended box
  *   (homogeneous Dirichlet conditions on all cut space and time faces,
  *   Eq. 10-12) and is factored by ILU(0) on its structural pattern.
- *   local        0 = ILU(0) (the only local solver of this version).
+ *   local        0 = ILU(0); 1 = exact LU with partial pivoting of every box
+ *                matrix, stored as a band in the box's natural point-block
+ *                order (FP64 only; for small boxes: at most 28,672 unknowns
+ *                and half-bandwidth 2,048 per box, else KKT_ERR_ARG, and the
+ *                bands must fit in 80 % of free device memory, else
+ *                KKT_ERR_NOMEM).
  *   factor_prec  64 = factor and solve in FP64, 32 = FP32, 16 = factor in FP32
  *                and store the factors as BF16 (round to nearest); the solve
  *                converts them to FP32 and accumulates in FP32.

@@ -106,12 +106,14 @@ class Problem:
 class RAS:
     """One-level space-time RAS with ILU(0) subdomain solves (ras_setup)."""
 
-    def __init__(self, prob: Problem, nsub: Sequence[int], overlap: int, factor_prec: int = 64):
+    def __init__(self, prob: Problem, nsub: Sequence[int], overlap: int, factor_prec: int = 64, local: str = "ilu0"):
+        """factor_prec 64, 32 or 16 (BF16 storage); local "ilu0" or "lu" (exact, FP64 only)."""
         self._lib = _lib.load()
         self.prob = prob
         ns = (C.c_int * 4)(*[int(v) for v in nsub])
         h = C.c_void_p()
-        check(self._lib.ras_setup(prob.h, ns, int(overlap), 0, int(factor_prec), C.byref(h)), "ras_setup")
+        loc = {"ilu0": 0, "lu": 1}[local]
+        check(self._lib.ras_setup(prob.h, ns, int(overlap), loc, int(factor_prec), C.byref(h)), "ras_setup")
         self.h = h
 
     def apply(self, r: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

@@ -18,35 +18,14 @@
 // of a finished row holds 1/u_kk.
 #pragma once
 
-#include "internal.cuh"
-#include "ras.cuh"
+#include "slotval.cuh"
 
 namespace {
 
 #include "ilu_rows.inc"
-#include "ilu_slots.inc"
-
-static_assert(kGenSlots == kSlots, "slot count");
-
-template <typename T>
-struct Coefs {
-  const T *S, *ST, *B, *K;
-};
-template <typename T>
-__device__ __forceinline__ Coefs<T> coefs(const DevProblem& p);
-template <>
-__device__ __forceinline__ Coefs<double> coefs<double>(const DevProblem& p) {
-  return {p.S, p.ST, p.B, p.K};
-}
-template <>
-__device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
-  return {p.S32, p.ST32, p.B32, p.K32};
-}
 
 constexpr int kGatherThreads = 256;
 constexpr int kFactorThreads = 256;
-// diagonal slots of the C, G and f rows
-constexpr int kDiagC = 80, kDiagG = 122, kDiagF = 245;
 
 // One thread per point (wavefront order, so the threads of a chunk write
 // consecutive addresses); all threads of a warp on the same slot.  Entries are
@@ -63,42 +42,12 @@ __global__ void __launch_bounds__(kGatherThreads) gather_chunks(DevProblem p, co
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= bx.P) return;
   const Coefs<T> cf = coefs<T>(p);
-  const int lex = perm[bx.poff + q];
-  const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-  const int kt = lex / (bx.lx * bx.ly * bx.lz);
+  const PointRow<T> pr = point_row<T>(p, bx, perm[bx.poff + q]);
   const int2 pt = ptab[bx.poff + q];
   T* dst = Fb + pt.x;
-  const int gx = bx.x0 + kx, gy = bx.y0 + ky, gz = bx.z0 + kz, n = bx.t0 + kt;
-  const int j = gx + p.nx * (gy + p.ny * gz);
-  const bool dirj = p.dir[j] != 0;
-  const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta), b1 = (T)p.beta1, b2 = (T)p.beta2;
-  const T sj = (T)p.sens[j];
-  // time weights of the f row at this level
-  const T mt0 = (n > 0 ? tau / (T)3 : (T)0) + (n < p.M ? tau / (T)3 : (T)0);
-  const T lt0 = (n > 0 ? (T)1 / tau : (T)0) + (n < p.M ? (T)1 / tau : (T)0);
-  const T mt1 = tau / (T)6, lt1 = -(T)1 / tau;
   for (int s = 0; s < kSlots; ++s) {
-    const int dt = c_gen_slot[s][0], dz = c_gen_slot[s][1], dy = c_gen_slot[s][2], dx = c_gen_slot[s][3];
-    const int cc = c_gen_slot[s][4];
-    const int ax = kx + dx, ay = ky + dy, az = kz + dz, at = kt + dt;
-    T v = 0;
-    if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt) {
-      const int d = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-      const size_t ci = (size_t)d * p.N + j;
-      if (s < kGenRowSlots0) {
-        if (n == 0 || dirj) v = (s == kDiagC) ? (T)1 : (T)0;
-        else if (cc == 0) v = dt == 0 ? cf.B[ci] + th * tau * cf.S[ci] : -cf.B[ci] + th1 * tau * cf.S[ci];
-        else v = dt == 0 ? -th * tau * cf.B[ci] : -th1 * tau * cf.B[ci];
-      } else if (s < kGenRowSlots0 + kGenRowSlots1) {
-        if (n == p.M || dirj) v = (s == kDiagG) ? (T)1 : (T)0;
-        else if (cc == 1) v = dt == 0 ? cf.B[ci] + th * tau * cf.ST[ci] : -cf.B[ci] + th1 * tau * cf.ST[ci];
-        else v = (dt == 0 ? th1 : th) * tau * sj;
-      } else {
-        const T mt = dt == 0 ? mt0 : mt1, lt = dt == 0 ? lt0 : lt1;
-        v = cc == 1 ? -mt * cf.B[ci] : b1 * lt * cf.B[ci] + b2 * mt * cf.K[ci];
-      }
-    }
-    dst[(long long)c_gen_rank[s] * pt.y] = v;
+    bool inb;
+    dst[(long long)c_gen_rank[s] * pt.y] = slot_value<T>(p, bx, cf, pr, s, &inb);
   }
 }
 

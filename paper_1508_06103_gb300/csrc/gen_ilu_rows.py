@@ -167,6 +167,18 @@ def generate() -> str:
     for a in range(0, len(slots), 20):
         hdr.append("    " + ", ".join(str(r) for r in rank[a:a + 20]) + ",")
     hdr.append("};")
+    hdr.append("#ifdef __CUDACC__")
+    hdr.append("// per slot: level offset dt, spatial offsets dz, dy, dx and column component")
+    hdr.append("__constant__ signed char c_gen_slot[%d][5] = {" % len(slots))
+    for a in range(0, len(slots), 8):
+        hdr.append("    " + ", ".join("{%d, %d, %d, %d, %d}" % sl for sl in slots[a:a + 8]) + ",")
+    hdr.append("};")
+    hdr.append("// rank of each slot in a chunk block (device copy of kGenRank)")
+    hdr.append("__constant__ short c_gen_rank[%d] = {" % len(slots))
+    for a in range(0, len(slots), 20):
+        hdr.append("    " + ", ".join(str(r) for r in rank[a:a + 20]) + ",")
+    hdr.append("};")
+    hdr.append("#endif")
     hdr.append("")
     out = [
         "// Generated by gen_ilu_rows.py from the KKT row stencils -- do not edit by hand.",
@@ -174,18 +186,6 @@ def generate() -> str:
         "// on the chunk layout (slot s of a point at offset kGenRank[s] * stride).",
         "#pragma once",
         "",
-        "// per slot: level offset dt, spatial offsets dz, dy, dx and column component",
-        "__constant__ signed char c_gen_slot[%d][5] = {" % len(slots),
-    ]
-    for a in range(0, len(slots), 8):
-        out.append("    " + ", ".join("{%d, %d, %d, %d, %d}" % sl for sl in slots[a:a + 8]) + ",")
-    out.append("};")
-    out.append("// rank of each slot in a chunk block (device copy of kGenRank)")
-    out.append("__constant__ short c_gen_rank[%d] = {" % len(slots))
-    for a in range(0, len(slots), 20):
-        out.append("    " + ", ".join(str(r) for r in rank[a:a + 20]) + ",")
-    out += [
-        "};",
         f"constexpr int kGenNbrs = {len(nbrs)};",
         "// pivot point offsets (dt, dz, dy, dx) shared by the three row types",
         "__constant__ signed char c_gen_nbr[%d][4] = {" % len(nbrs),

@@ -498,8 +498,12 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       set_error("ras_setup: each nsub must lie in [1, points along that axis]");
       return KKT_ERR_ARG;
     }
-  if (overlap < 0 || local != 0 || (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
-    set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)), factor_prec 64, 32 or 16");
+  if (overlap < 0 || (local != 0 && local != 1) || (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
+    set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)) or 1 (exact LU), factor_prec 64, 32 or 16");
+    return KKT_ERR_ARG;
+  }
+  if (local == 1 && factor_prec != 64) {
+    set_error("ras_setup: the exact local LU is FP64 only (factor_prec 64)");
     return KKT_ERR_ARG;
   }
   const SlotTables& T = tables();
@@ -541,6 +545,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (!m) return KKT_ERR_NOMEM;
   m->prob = p;
   m->prec = factor_prec;
+  m->local = local;
   auto stride = [&](int n) {
     return factor_prec == 64 ? chunk_stride<double>(n)
                              : (factor_prec == 32 ? chunk_stride<float>(n) : chunk_stride<__nv_bfloat16>(n));
@@ -656,6 +661,20 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
             return KKT_ERR_ARG;
           }
           foff += off;
+          if (local == 1) {
+            // exact LU: band of the box matrix in natural point-block order
+            const long long n_b = 3 * b.P;
+            b.kl = 3 * (1 + b.lx + b.lx * b.ly + b.lx * b.ly * b.lz) + 2;
+            if (b.kl > kMaxLuBand || n_b > kMaxLuUnknowns) {
+              set_error("ras_setup: a subdomain is too large for the exact local LU (at most " +
+                        std::to_string(kMaxLuUnknowns) + " unknowns and half-bandwidth " +
+                        std::to_string(kMaxLuBand) + "); use ILU(0) or more subdomains");
+              delete m;
+              return KKT_ERR_ARG;
+            }
+            b.aoff = m->ab_count;
+            m->ab_count += n_b * (3LL * b.kl + 1);
+          }
           boxes.push_back(b);
         }
   m->nbox = (int)boxes.size();
@@ -697,6 +716,22 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       (factor_prec == 16 && cudaMalloc(&m->Ffac, foff * sizeof(float)) != cudaSuccess) ||
       cudaMalloc(&m->status, sizeof(int)) != cudaSuccess)
     return fail(KKT_ERR_NOMEM, "device allocation failed");
+  if (local == 1) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(KKT_ERR_CUDA, "cudaMemGetInfo failed");
+    const double need = (double)m->ab_count * sizeof(double);
+    if (need > 0.8 * (double)free_b)
+      return fail(KKT_ERR_NOMEM, ("the exact local LU needs " + std::to_string((long long)(need / 1e6)) +
+                                  " MB of band storage; use ILU(0) or more subdomains").c_str());
+    if (cudaMalloc(&m->AB, m->ab_count * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->ipiv, 3 * perm.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&m->lu_ju, 2 * boxes.size() * sizeof(int)) != cudaSuccess)
+      return fail(KKT_ERR_NOMEM, "device allocation failed (exact LU)");
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    m->lu_ctas = std::max(1, std::min(64, nsm / std::max(1, m->nbox)));   // one wave of 1024-thread CTAs
+  }
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpy(m->boxes, boxes.data(), boxes.size() * sizeof(BoxDesc), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -746,7 +781,8 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename Sol
 
 kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
-  if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
+  if (m->local == 1) KKT_TRY(ras_lu_factor(m, s));
+  else if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
   else if (m->prec == 32) KKT_TRY(ras_factor_launch32(m, s));
   else KKT_TRY(ras_factor_launch16(m, s));
   int st = 0;
@@ -761,6 +797,7 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
 
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s) {
   TimedScope timed(&m->timing, s);
+  if (m->local == 1) return ras_lu_solve(m, r, z, s);
   if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s);
   if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s);
   return launch_solve<__nv_bfloat16>(m, r, z, (float*)m->V, s);
@@ -814,7 +851,7 @@ extern "C" kkt_status ras_info(const ras_precond* m, int* nbox, long long* point
   for (const BoxDesc& b : m->boxes_h) pts += b.P;
   if (nbox) *nbox = m->nbox;
   if (points) *points = pts;
-  if (factor_values) *factor_values = m->fcount;
+  if (factor_values) *factor_values = m->local == 1 ? m->ab_count : m->fcount;
   if (value_bytes) *value_bytes = m->prec == 64 ? 8 : (m->prec == 32 ? 4 : 2);
   return KKT_OK;
 }
@@ -856,6 +893,9 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->lptr);
   cudaFree(m->ptab);
   cudaFree(m->Ffac);
+  cudaFree(m->AB);
+  cudaFree(m->ipiv);
+  cudaFree(m->lu_ju);
   cudaFree(m->chunks);
   cudaFree(m->F);
   cudaFree(m->V);
@@ -907,6 +947,10 @@ extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* 
   }
   if (r == z) {
     set_error("ras_apply_static: r and z must not overlap");
+    return KKT_ERR_ARG;
+  }
+  if (m->local != 0) {
+    set_error("ras_apply_static: only ILU(0) preconditioners have a static-scratch apply; use ras_apply");
     return KKT_ERR_ARG;
   }
   const size_t bytes = (size_t)m->vcount * (m->prec == 64 ? sizeof(double) : sizeof(float));

@@ -31,7 +31,14 @@ struct BoxDesc {
   long long poff;              // offset into perm / iperm
   long long loff;              // offset into the wavefront pointers
   int cbeg, cend;              // chunk range
+  int kl;                      // exact LU: half-bandwidth of the box matrix
+  long long aoff;              // exact LU: offset of the box's band (elements)
 };
+
+// exact LU: largest half-bandwidth and box size (the solve keeps a box's
+// vector in shared memory)
+constexpr int kMaxLuBand = 2048;
+constexpr int kMaxLuUnknowns = 28672;
 
 struct ras_precond {
   kkt_problem* prob = nullptr;
@@ -57,6 +64,12 @@ struct ras_precond {
   void* Ffac = nullptr;        // BF16 storage: the FP32 values the factorisation works on
   void* V = nullptr;           // padded local vectors
   int* status = nullptr;
+  int local = 0;               // 0: ILU(0) local solves, 1: exact banded LU (FP64)
+  double* AB = nullptr;        // exact LU: band factors of all boxes
+  long long ab_count = 0;
+  int* ipiv = nullptr;         // exact LU: row interchanges (3 per box point)
+  int* lu_ju = nullptr;        // exact LU: per box, last column reached by fill (two slots)
+  int lu_ctas = 1;             // exact LU: CTAs per box in an elimination step
   TimingLog timing;            // subdomain-solve launches
   TimingLog factor_timing;     // ILU(0) factorisation launches
 };
@@ -68,5 +81,8 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s);
 kkt_status ras_factor_launch32(ras_precond* m, cudaStream_t s);
 kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s);
 kkt_status ras_factor_launch16(ras_precond* m, cudaStream_t s);   // FP32 factorisation, BF16 store
+// exact banded LU (lu.cu)
+kkt_status ras_lu_factor(ras_precond* m, cudaStream_t s);
+kkt_status ras_lu_solve(ras_precond* m, const double* r, double* z, cudaStream_t s);
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s);
 kkt_status ras_check(ras_precond* m);

@@ -7,8 +7,9 @@
   mixed forms, solved to 1e-10, agree with the FP64 form's to 1e-5 relative
   L2 (the benchmark spec's bound for the mixed form).
 * 8^3 cells x 16 implicit-Euler steps (37,179 unknowns), one-level RAS
-  2x2x2x2, overlap 1: the GPU solution agrees with the oracle's solution of
-  the same system to 1e-8 relative after both are solved to 1e-13.
+  2x2x2x2, overlap 1, exact local LU (and ILU(0)): the GPU solution agrees
+  with the oracle's solution of the same system to 1e-8 relative after both
+  are solved to 1e-13.
 """
 
 import os
@@ -95,10 +96,14 @@ def test_tiny_implicit_euler_one_level_matches_oracle(api):
     sol = okry.gmres(lambda u: F @ u, b, ref.apply, restart=30, rtol=1e-13, maxit=400)
     assert sol.converged
     prob = api.Problem.from_workload(w)
-    ras = api.RAS(prob, w.nsub, w.overlap, 64)
     bd = prob.rhs(torch.from_numpy(cobs).cuda())
     assert np.allclose(bd.cpu().numpy(), b, rtol=1e-14, atol=1e-18)
-    x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, restart=30, rtol=1e-13, maxit=3000)
-    assert st == 0
-    xe = x.cpu().numpy()
-    assert np.linalg.norm(xe - sol.x) <= 1e-8 * np.linalg.norm(sol.x)
+    # the configuration's exact local LU, and ILU(0) local solves
+    for local in ("lu", "ilu0"):
+        ras = api.RAS(prob, w.nsub, w.overlap, 64, local=local)
+        x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, restart=30, rtol=1e-13, maxit=3000)
+        assert st == 0
+        xe = x.cpu().numpy()
+        assert np.linalg.norm(xe - sol.x) <= 1e-8 * np.linalg.norm(sol.x)
+        if local == "lu":
+            assert its <= sol.iterations + 2  # the same preconditioner as the oracle's

@@ -1,6 +1,9 @@
 """GPU parity of the Schwarz preconditioners and the (F)GMRES solves against the oracle.
 
 Tolerances:
+* one-level RAS with exact local LU: both sides solve the box matrices
+  exactly; max|dz| <= 100 cond_1(M_ij) u max|z| (largest cond_1 of the boxes,
+  computed in the test; 3e5 at most on these cases).
 * one-level RAS, FP64 factors: the GPU and the oracle run the same ILU(0)
   (same pattern, same IKJ update order) and the same triangular sweeps, so
   they differ only by rounding order; relative to max|z| the difference is
@@ -66,6 +69,37 @@ def test_ras_apply_fp64_matches_oracle(api, case):
         z = ras.apply(_dev(r)).cpu().numpy()
         zr = ref.apply(r)
         assert np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
+
+
+@pytest.mark.parametrize("case", RAS_CASES, ids=["2x2x1x2", "3x2x2x3-ov2", "single"])
+def test_ras_apply_exact_lu_matches_oracle(api, case):
+    # Both sides solve the same box matrices exactly (GPU: band LU with partial
+    # pivoting; oracle: sparse LU), each backward stable, so each box's
+    # solution differs by at most ~cond_1(M_ij) u times a modest growth factor:
+    # bar 100 cond_1 u max|z| with the largest cond_1 of the boxes.
+    w = W.random_small(nsens=6, **case["w"])
+    p = okkt.Problem.from_workload(w)
+    F = okkt.assemble(p)
+    ref = osch.RAS(p, F, case["nsub"], case["ov"], "lu")
+    kappa = max(np.linalg.cond(F[idx][:, idx].toarray(), 1) for idx in ref.idx)
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, case["nsub"], case["ov"], 64, local="lu")
+    for seed in (1, 2):
+        r = W.random_vector(prob.n, seed)
+        z = ras.apply(_dev(r)).cpu().numpy()
+        zr = ref.apply(r)
+        assert np.abs(z - zr).max() <= 100 * kappa * 2.0**-53 * np.abs(zr).max()
+
+
+def test_exact_lu_rejects_other_precisions_and_static_apply(api):
+    case = RAS_CASES[0]
+    w = W.random_small(nsens=6, **case["w"])
+    prob = api.Problem.from_workload(w)
+    with pytest.raises(Exception, match="FP64 only"):
+        api.RAS(prob, case["nsub"], case["ov"], 32, local="lu")
+    ras = api.RAS(prob, case["nsub"], case["ov"], 64, local="lu")
+    with pytest.raises(Exception, match="ILU"):
+        ras.apply_static(_dev(W.random_vector(prob.n, 1)))
 
 
 def test_ras_apply_fp32_close_to_oracle(api):
