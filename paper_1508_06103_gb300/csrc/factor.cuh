@@ -25,7 +25,7 @@ namespace {
 #include "ilu_rows.inc"
 
 constexpr int kGatherThreads = 256;
-constexpr int kFactorThreads = 256;
+constexpr int kFactorThreads = 128;   // two CTAs per SM: all 256 boxes resident at once
 
 // One thread per point (wavefront order, so the threads of a chunk write
 // consecutive addresses); all threads of a warp on the same slot.  Entries are
@@ -56,7 +56,7 @@ __device__ __forceinline__ void check_pivot(double d, int* status) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFactorThreads, 1) ilu0_factor(const BoxDesc* __restrict__ boxes,
+__global__ void __launch_bounds__(kFactorThreads, 2) ilu0_factor(const BoxDesc* __restrict__ boxes,
                                                                  const int* __restrict__ iperm,
                                                                  const int* __restrict__ perm,
                                                                  const int* __restrict__ lptr,

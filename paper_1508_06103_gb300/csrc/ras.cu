@@ -132,28 +132,43 @@ int slot_rank(int s) {
   return kLRanks + 70 + (s - kFDiag);
 }
 
-template <typename T>
+// Chunk configurations of the subdomain solve, per stored type S and lanes
+// per point L: candidate chunk sizes (points) and the row-stride rule
+// cp = R (mod Q) that makes the L-lane shared-memory reads of a chunk block
+// free of bank conflicts (the lanes of a warp cover 32/L points and L rows).
+template <typename S, int L>
 struct ChunkCfg;
 template <>
-struct ChunkCfg<float> {
-  static constexpr int CH = 56;       // points per chunk (4 lanes each: 7 full warps)
-  static constexpr int CH2 = 40, CH3 = 24;   // smaller chunks (row strides 40, 24) for small boxes
-  static constexpr int Q = 16, R = 8; // row stride cp = 8 (mod 16): conflict-free 4-lane reads
+struct ChunkCfg<float, 4> {
+  static constexpr int CH = 56, CH2 = 40, CH3 = 24;   // 7 / 5 / 3 full warps
+  static constexpr int Q = 16, R = 8;                  // cp = 8 (mod 16)
 };
 template <>
-struct ChunkCfg<double> {
-  static constexpr int CH = 32;       // 4 full warps
-  static constexpr int CH2 = 20, CH3 = 12;   // smaller chunks (row strides 20, 12)
-  static constexpr int Q = 8, R = 4;  // cp = 4 (mod 8)
+struct ChunkCfg<float, 8> {
+  static constexpr int CH = 28, CH2 = 20, CH3 = 12;   // 7 / 5 / 3 full warps
+  static constexpr int Q = 8, R = 4;                   // cp = 4 (mod 8)
 };
-
 template <>
-struct ChunkCfg<__nv_bfloat16> {     // FP32 factors stored as BF16
-  static constexpr int CH = 80;       // 10 full warps
-  static constexpr int CH2 = 48, CH3 = 16;
-  static constexpr int Q = 32, R = 16; // cp = 16 (mod 32): two values per bank word, conflict-free
+struct ChunkCfg<double, 4> {
+  static constexpr int CH = 32, CH2 = 20, CH3 = 12;
+  static constexpr int Q = 8, R = 4;                   // cp = 4 (mod 8)
 };
-
+template <>
+struct ChunkCfg<__nv_bfloat16, 4> {                   // FP32 factors stored as BF16
+  static constexpr int CH = 80, CH2 = 48, CH3 = 16;
+  static constexpr int Q = 32, R = 16;                 // cp = 16 (mod 32): two values per bank word
+};
+// lanes-per-point variants compiled for each stored type
+template <typename S>
+struct LaneSet {
+  static constexpr int N = 1;
+  static constexpr int lanes[1] = {4};
+};
+template <>
+struct LaneSet<float> {
+  static constexpr int N = 2;
+  static constexpr int lanes[2] = {4, 8};
+};
 // arithmetic type of the solve for a storage type (BF16 factors: FP32)
 template <typename S>
 struct SolveArith {
@@ -172,10 +187,15 @@ __device__ __forceinline__ float arith<float, __nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
 
-template <typename T>
+template <typename S, int L>
 int chunk_stride(int n) {
-  const int Q = ChunkCfg<T>::Q, R = ChunkCfg<T>::R;
+  const int Q = ChunkCfg<S, L>::Q, R = ChunkCfg<S, L>::R;
   return n <= R ? R : R + ((n - R + Q - 1) / Q) * Q;
+}
+int chunk_stride_of(int prec, int lanes, int n) {
+  if (prec == 64) return chunk_stride<double, 4>(n);
+  if (prec == 16) return chunk_stride<__nv_bfloat16, 4>(n);
+  return lanes == 8 ? chunk_stride<float, 8>(n) : chunk_stride<float, 4>(n);
 }
 
 // ---------------------------------------------------------------------------
@@ -227,39 +247,38 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned pari
 
 // ---------------------------------------------------------------------------
 // Subdomain solve z = sum_boxes (R^0)^T M^{-1} R^delta r: one CTA per box,
-// kLanes lanes per point, one chunk of points per step.  Each lane takes every
-// kLanes-th row of the chunk's block in shared memory; the loops have
+// LANES lanes per point, one chunk of points per step.  Each lane takes every
+// LANES-th row of the chunk's block in shared memory; the loops have
 // compile-time trip counts and a shuffle reduction closes each row.
 // With SMEM the box's padded local vector lives in shared memory as well.
 // ---------------------------------------------------------------------------
-constexpr int kLanes = 4;
 constexpr size_t kSmemLimit = 227 * 1024;          // dynamic shared memory of one CTA
 constexpr int kSolveHeader = 2048;   // off[] table (326 ints) and, from byte 1536, the mbarriers
 constexpr int kMaxStages = 4;        // buffers of the subdomain solve's copy ring
 
-// sum over block rows [R0, R1) of B[r*cp + j] * vp[off[r + SOFF]]
-template <int R0, int R1, int SOFF, typename S, typename T>
+// sum over block rows [R0, R1) of B[r*cp + j] * vp[off[r + SOFF]]; L lanes per point
+template <int R0, int R1, int SOFF, int L, typename S, typename T>
 __device__ __forceinline__ T row_dot(const S* __restrict__ B, int cp, int j, const int* __restrict__ off,
                                      const T* vp, int lane, bool act) {
   T acc = 0;
 #pragma unroll
-  for (int k = 0; k < (R1 - R0 + kLanes - 1) / kLanes; ++k) {
-    const int r = R0 + lane + k * kLanes;
+  for (int k = 0; k < (R1 - R0 + L - 1) / L; ++k) {
+    const int r = R0 + lane + k * L;
     if (act && r < R1) acc += arith<T>(B[r * cp + j]) * vp[off[r + SOFF]];
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
 }
 
 // S: type of the stored factor values; T: arithmetic and local-vector type
-template <typename S, bool SMEM>
-__global__ void __launch_bounds__(ChunkCfg<S>::CH * kLanes) ras_solve(
+template <typename S, bool SMEM, int kL>
+__global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
     const BoxDesc* __restrict__ boxes, const int* __restrict__ perm, const Chunk* __restrict__ chunks,
     const S* __restrict__ F, typename SolveArith<S>::type* __restrict__ V, const double* __restrict__ r,
     double* __restrict__ z, int nx, int ny, int N, int bstride, int nstage, int* __restrict__ status) {
   using T = typename SolveArith<S>::type;
-  static_assert((ChunkCfg<S>::CH * kLanes) % 32 == 0, "the solve needs full warps");
+  static_assert(kL == 4 || kL == 8, "lanes per point");
   extern __shared__ __align__(128) unsigned char smem[];
   int* off = reinterpret_cast<int*>(smem);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
@@ -315,7 +334,7 @@ __global__ void __launch_bounds__(ChunkCfg<S>::CH * kLanes) ras_solve(
     v[pq + 2] = (T)r[g + 2];
   }
   __syncthreads();
-  const int lane = threadIdx.x & (kLanes - 1), j = threadIdx.x / kLanes;
+  const int lane = threadIdx.x & (kL - 1), j = threadIdx.x / kL;
   // padded-vector offset of this thread's point from its lexicographic index
   auto point_offset = [&](int lex) -> long long {
     const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
@@ -361,9 +380,9 @@ __global__ void __launch_bounds__(ChunkCfg<S>::CH * kLanes) ras_solve(
       // own-C slot (block row 93) and the f row's own-G slot (row 174), so the
       // three rows' sums over other points are gathered together and the two
       // own-point terms are applied afterwards in C, G, f order.
-      const T aC = row_dot<0, 80, 0>(B, c.cp, j, off, vp, lane, act);
-      const T aG = row_dot<80, 93, 28>(B, c.cp, j, off, vp, lane, act);
-      const T aF = row_dot<94, 174, 70>(B, c.cp, j, off, vp, lane, act);
+      const T aC = row_dot<0, 80, 0, kL>(B, c.cp, j, off, vp, lane, act);
+      const T aG = row_dot<80, 93, 28, kL>(B, c.cp, j, off, vp, lane, act);
+      const T aF = row_dot<94, 174, 70, kL>(B, c.cp, j, off, vp, lane, act);
       if (act && lane == 0) {
         const T yc = v0 - aC;
         const T yg = v1 - aG - arith<T>(B[93 * c.cp + j]) * yc;
@@ -376,9 +395,9 @@ __global__ void __launch_bounds__(ChunkCfg<S>::CH * kLanes) ras_solve(
       // Every U-slot reads a point of a later wavefront except the C row's
       // own-f slot (U block row 1), applied after the f row is solved.  The
       // diagonal rows 0, 28, 70 hold the reciprocals of the pivots.
-      const T bF = row_dot<71, 151, 175>(B, c.cp, j, off, vp, lane, act);
-      const T bG = row_dot<29, 70, 94>(B, c.cp, j, off, vp, lane, act);
-      const T bC = row_dot<2, 28, 80>(B, c.cp, j, off, vp, lane, act);
+      const T bF = row_dot<71, 151, 175, kL>(B, c.cp, j, off, vp, lane, act);
+      const T bG = row_dot<29, 70, 94, kL>(B, c.cp, j, off, vp, lane, act);
+      const T bC = row_dot<2, 28, 80, kL>(B, c.cp, j, off, vp, lane, act);
       if (act && lane == 0) {
         const T zf = (v2 - bF) * arith<T>(B[70 * c.cp + j]);
         const T zg = (v1 - bG) * arith<T>(B[28 * c.cp + j]);
@@ -448,37 +467,55 @@ size_t solve_smem(int cpmax, int nstage, size_t esz, size_t vsz, long long max_p
 // fewest waves of CTAs over the SMs (the runtime's occupancy for the shared
 // memory, threads and registers); the shallowest ring (a deeper ring takes
 // shared memory from the L1 that caches a global local vector, and lost
-// 30-45 % in every case measured); the largest chunk (fewest steps).
+// 30-45 % in every case measured); in FP32, 8 lanes per point when the
+// vector is in shared memory (0.28 vs 0.45 ms on the coarse-sized boxes) and
+// 4 when it is in global memory (3.95 vs 4.37 ms at 32^3 x 64); the largest
+// chunk (fewest steps).
 struct SolveShape {
-  int ch, cpmax, nstage;
+  int ch, cpmax, nstage, lanes;
   bool smem_vec;
 };
-template <typename T>
-kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, SolveShape* out) {
-  const int cands[3] = {ChunkCfg<T>::CH, ChunkCfg<T>::CH2, ChunkCfg<T>::CH3};
-  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-  SolveShape best{ChunkCfg<T>::CH, chunk_stride<T>(ChunkCfg<T>::CH), 2, false};
-  long long best_key = -1;
+template <typename T, bool SMEM, int L>
+const void* solve_kernel() {
+  return (const void*)ras_solve<T, SMEM, L>;
+}
+template <typename T, int L>
+kkt_status shape_candidates(int nbox, long long max_pad, int nsm, SolveShape* best, long long* best_key) {
+  const int cands[3] = {ChunkCfg<T, L>::CH, ChunkCfg<T, L>::CH2, ChunkCfg<T, L>::CH3};
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemLimit));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemLimit));
   for (int ci = 0; ci < 3; ++ci)
     for (int ns = 2; ns <= kMaxStages; ++ns)
       for (int sv = 1; sv >= 0; --sv) {
-        const int ch = cands[ci], cp = chunk_stride<T>(ch);
+        const int ch = cands[ci], cp = chunk_stride<T, L>(ch);
         const size_t sm = solve_smem(cp, ns, sizeof(T), sizeof(typename SolveArith<T>::type), max_pad, sv != 0);
         if (sm > kSmemLimit) continue;
-        const int threads = (ch * kLanes + 31) / 32 * 32;
+        const int threads = (ch * L + 31) / 32 * 32;
         int per_sm = 0;
         KKT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sv ? (const void*)ras_solve<T, true> : (const void*)ras_solve<T, false>, threads, sm));
+            &per_sm, sv ? solve_kernel<T, true, L>() : solve_kernel<T, false, L>(), threads, sm));
         if (per_sm < 1) continue;
         const long long waves = (nbox + (long long)nsm * per_sm - 1) / ((long long)nsm * per_sm);
-        // smaller key is better
-        const long long key = (sv ? 0 : 1000000000LL) + waves * 100000 + (ns - 2) * 1000 + (100 - ch);
-        if (best_key < 0 || key < best_key) {
-          best_key = key;
-          best = SolveShape{ch, cp, ns, sv != 0};
+        // smaller key is better; with the vector in shared memory 8 lanes per
+        // point, with the vector in global memory 4 (measured, see above)
+        const int lane_pref = sv ? (L == 8 ? 0 : 1) : (L == 4 ? 0 : 1);
+        const long long key =
+            (sv ? 0 : 1000000000LL) + waves * 100000 + (ns - 2) * 1000 + lane_pref * 100 + (100 - ch);
+        if (*best_key < 0 || key < *best_key) {
+          *best_key = key;
+          *best = SolveShape{ch, cp, ns, L, sv != 0};
         }
       }
+  return KKT_OK;
+}
+template <typename T>
+kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, SolveShape* out) {
+  SolveShape best{ChunkCfg<T, 4>::CH, chunk_stride<T, 4>(ChunkCfg<T, 4>::CH), 2, 4, false};
+  long long best_key = -1;
+  KKT_TRY((shape_candidates<T, 4>(nbox, max_pad, nsm, &best, &best_key)));
+  if constexpr (LaneSet<T>::N > 1) KKT_TRY((shape_candidates<T, 8>(nbox, max_pad, nsm, &best, &best_key)));
   *out = best;
   return KKT_OK;
 }
@@ -546,10 +583,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   m->prob = p;
   m->prec = factor_prec;
   m->local = local;
-  auto stride = [&](int n) {
-    return factor_prec == 64 ? chunk_stride<double>(n)
-                             : (factor_prec == 32 ? chunk_stride<float>(n) : chunk_stride<__nv_bfloat16>(n));
-  };
+  auto stride = [&](int n) { return chunk_stride_of(factor_prec, m->lanes, n); };
   std::vector<std::pair<int, int>> pr[4];
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   {
@@ -582,6 +616,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     m->cpmax = sh.cpmax;
     m->smem_vec = sh.smem_vec;
     m->nstage = sh.nstage;
+    m->lanes = sh.lanes;
   }
   const int CH = m->ch;
   std::vector<BoxDesc> boxes;
@@ -755,26 +790,33 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
 
 namespace {
 
-template <typename S>
-kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
-                        cudaStream_t s) {
+template <typename S, int L>
+kkt_status launch_solve_l(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
+                          cudaStream_t s) {
   using T = typename SolveArith<S>::type;
   const kkt_problem* p = m->prob;
-  const int threads = (m->ch * kLanes + 31) / 32 * 32;
+  const int threads = (m->ch * L + 31) / 32 * 32;
   const int bstride = kLRanks * m->cpmax;
   const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(S), sizeof(T), m->max_pad, m->smem_vec);
   if (m->smem_vec) {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<S, true><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
-                                                      p->nx, p->ny, p->N, bstride, m->nstage, m->status);
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, true, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ras_solve<S, true, L><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
+                                                         p->nx, p->ny, p->N, bstride, m->nstage, m->status);
   } else {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<S, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
-                                                       p->nx, p->ny, p->N, bstride, m->nstage, m->status);
+    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, false, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ras_solve<S, false, L><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
+                                                          p->nx, p->ny, p->N, bstride, m->nstage, m->status);
   }
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
+}
+template <typename S>
+kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
+                        cudaStream_t s) {
+  if constexpr (LaneSet<S>::N > 1)
+    if (m->lanes == 8) return launch_solve_l<S, 8>(m, r, z, V, s);
+  return launch_solve_l<S, 4>(m, r, z, V, s);
 }
 
 }  // namespace

@@ -48,6 +48,7 @@ struct ras_precond {
   int cpmax = 0;               // largest chunk row stride
   bool smem_vec = false;       // solve keeps the local vectors in shared memory
   int nstage = 2;              // buffers of the solve's copy ring
+  int lanes = 4;               // lanes per point in the solve
   long long fcount = 0;        // factor values
   long long max_pad = 0;       // largest padded local vector (elements)
   long long vcount = 0;        // elements of all padded local vectors (the solve's scratch)
