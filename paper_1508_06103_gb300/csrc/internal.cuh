@@ -60,6 +60,7 @@ struct DevProblem {
   int nx, ny, nz, N, M, L;
   long long P;                              // points N * (M+1)
   double tau, theta, beta1, beta2;
+  double hx, hy, hz;                        // mesh widths (B and K are tensor products of 1D factors)
   const double *S, *ST, *B, *K;             // [27][N] row coefficients (FP64)
   const float *S32, *ST32, *B32, *K32;      // FP32 copies
   const unsigned char* dir;                 // [N] 1 on Dirichlet nodes

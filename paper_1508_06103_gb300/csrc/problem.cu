@@ -91,6 +91,7 @@ DevProblem kkt_problem::dev() const {
   DevProblem d;
   d.nx = nx; d.ny = ny; d.nz = nz; d.N = N; d.M = M; d.L = L; d.P = P;
   d.tau = tau; d.theta = theta; d.beta1 = beta1; d.beta2 = beta2;
+  d.hx = hx; d.hy = hy; d.hz = hz;
   const size_t c = (size_t)kStencil * N;
   d.S = coef64; d.ST = coef64 + c; d.B = coef64 + 2 * c; d.K = coef64 + 3 * c;
   d.S32 = coef32; d.ST32 = coef32 + c; d.B32 = coef32 + 2 * c; d.K32 = coef32 + 3 * c;
