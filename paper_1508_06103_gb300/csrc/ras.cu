@@ -161,13 +161,11 @@ struct ChunkCfg<__nv_bfloat16, 4> {                   // FP32 factors stored as 
 // lanes-per-point variants compiled for each stored type
 template <typename S>
 struct LaneSet {
-  static constexpr int N = 1;
-  static constexpr int lanes[1] = {4};
+  static constexpr int N = 1;   // 4 lanes
 };
 template <>
 struct LaneSet<float> {
-  static constexpr int N = 2;
-  static constexpr int lanes[2] = {4, 8};
+  static constexpr int N = 2;   // 4 and 8 lanes
 };
 // arithmetic type of the solve for a storage type (BF16 factors: FP32)
 template <typename S>
@@ -256,15 +254,31 @@ constexpr size_t kSmemLimit = 227 * 1024;          // dynamic shared memory of o
 constexpr int kSolveHeader = 2048;   // off[] table (326 ints) and, from byte 1536, the mbarriers
 constexpr int kMaxStages = 4;        // buffers of the subdomain solve's copy ring
 
-// sum over block rows [R0, R1) of B[r*cp + j] * vp[off[r + SOFF]]; L lanes per point
-template <int R0, int R1, int SOFF, int L, typename S, typename T>
-__device__ __forceinline__ T row_dot(const S* __restrict__ B, int cp, int j, const int* __restrict__ off,
-                                     const T* vp, int lane, bool act) {
+// Row sums of a step, in two phases so that all neighbour gathers of the
+// step are issued before the first multiply-add uses one:
+//   gather<R0, R1, SOFF, L>  loads vp[off[r + SOFF]] for the lane's rows of [R0, R1)
+//   row_sum<R0, R1, L>       sum of B[r*cp + j] * value over those rows, reduced over the L lanes
+template <int R0, int R1, int L>
+struct RowSet {
+  static constexpr int K = (R1 - R0 + L - 1) / L;
+};
+template <int R0, int R1, int SOFF, int L, typename T>
+__device__ __forceinline__ void gather(T (&vals)[RowSet<R0, R1, L>::K], const int* __restrict__ off, const T* vp,
+                                       int lane, bool act) {
+#pragma unroll
+  for (int k = 0; k < RowSet<R0, R1, L>::K; ++k) {
+    const int r = R0 + lane + k * L;
+    vals[k] = (act && r < R1) ? vp[off[r + SOFF]] : (T)0;
+  }
+}
+template <int R0, int R1, int L, typename S, typename T>
+__device__ __forceinline__ T row_sum(const T (&vals)[RowSet<R0, R1, L>::K], const S* __restrict__ B, int cp, int j,
+                                     int lane) {
   T acc = 0;
 #pragma unroll
-  for (int k = 0; k < (R1 - R0 + L - 1) / L; ++k) {
+  for (int k = 0; k < RowSet<R0, R1, L>::K; ++k) {
     const int r = R0 + lane + k * L;
-    if (act && r < R1) acc += arith<T>(B[r * cp + j]) * vp[off[r + SOFF]];
+    if (r < R1) acc += arith<T>(B[r * cp + j]) * vals[k];
   }
 #pragma unroll
   for (int o = 1; o < L; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -273,10 +287,11 @@ __device__ __forceinline__ T row_dot(const S* __restrict__ B, int cp, int j, con
 
 // S: type of the stored factor values; T: arithmetic and local-vector type
 template <typename S, bool SMEM, int kL>
-__global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
+__global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
     const BoxDesc* __restrict__ boxes, const int* __restrict__ perm, const Chunk* __restrict__ chunks,
     const S* __restrict__ F, typename SolveArith<S>::type* __restrict__ V, const double* __restrict__ r,
-    double* __restrict__ z, int nx, int ny, int N, int bstride, int nstage, int* __restrict__ status) {
+    double* __restrict__ z, const int2* __restrict__ gtab, const int2* __restrict__ otab,
+    const int* __restrict__ vtab, int bstride, int nstage, int* __restrict__ status) {
   using T = typename SolveArith<S>::type;
   static_assert(kL == 4 || kL == 8, "lanes per point");
   extern __shared__ __align__(128) unsigned char smem[];
@@ -323,35 +338,26 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
     if (nstage - 1 < nblk) iss = ck[chunk_of(nstage - 1)];
   }
   // gather R^delta r into the padded local vector while the first blocks arrive
-  for (long long q = threadIdx.x; q < P; q += blockDim.x) {
-    const int kx = (int)(q % bx.lx), ky = (int)((q / bx.lx) % bx.ly), kz = (int)((q / (bx.lx * bx.ly)) % bx.lz);
-    const int kt = (int)(q / ((long long)bx.lx * bx.ly * bx.lz));
-    const long long g =
-        ((long long)(bx.t0 + kt) * N + (bx.x0 + kx) + (long long)nx * ((bx.y0 + ky) + (long long)ny * (bx.z0 + kz))) * 3;
-    const long long pq = 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
-    v[pq] = (T)r[g];
-    v[pq + 1] = (T)r[g + 1];
-    v[pq + 2] = (T)r[g + 2];
+  // (gtab: per box point, its global unknown index and its padded offset)
+  for (int q = threadIdx.x; q < (int)P; q += blockDim.x) {
+    const int2 e = gtab[bx.poff + q];
+    v[e.y] = (T)r[e.x];
+    v[e.y + 1] = (T)r[e.x + 1];
+    v[e.y + 2] = (T)r[e.x + 2];
   }
   __syncthreads();
   const int lane = threadIdx.x & (kL - 1), j = threadIdx.x / kL;
-  // padded-vector offset of this thread's point from its lexicographic index
-  auto point_offset = [&](int lex) -> long long {
-    const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
-    const int kt = lex / (bx.lx * bx.ly * bx.lz);
-    return 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
-  };
   // Step g works on the chunk of block g (`cur`).  The descriptor of the
   // chunk after next and the point index of the next chunk are loaded one
   // step ahead, so the only loads left between a barrier and the arithmetic
   // are the vector's.  Steps 0..nch-1 are the forward sweep with the unit
   // lower factor, steps nch..2 nch-1 the backward sweep with the upper factor.
   Chunk cur, nxt;
-  int lex_cur = 0;
+  int vq_cur = 0;
   if (nblk > 0) {
     cur = ck[0];
     nxt = ck[chunk_of(min(1, nblk - 1))];
-    lex_cur = j < cur.n ? perm[bx.poff + cur.q0 + j] : 0;
+    vq_cur = j < cur.n ? vtab[bx.poff + cur.q0 + j] : 0;
   }
   // one step of either sweep
   auto step = [&](int g, auto upper_tag) {
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
       if (g + nstage < nblk) iss = ck[chunk_of(g + nstage)];
     }
     const Chunk nn = ck[chunk_of(min(g + 2, nblk - 1))];
-    const int lex_nxt = (g + 1 < nblk && j < nxt.n) ? perm[bx.poff + nxt.q0 + j] : 0;
+    const int vq_nxt = (g + 1 < nblk && j < nxt.n) ? vtab[bx.poff + nxt.q0 + j] : 0;
     mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status);
     const Chunk& c = cur;
     const S* B = buf0 + (size_t)b * bstride;
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
     T* vp = v;
     T v0 = 0, v1 = 0, v2 = 0;
     if (act) {
-      vp = v + point_offset(lex_cur);
+      vp = v + vq_cur;
       v0 = vp[0];
       v1 = vp[1];
       v2 = vp[2];
@@ -380,9 +386,13 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
       // own-C slot (block row 93) and the f row's own-G slot (row 174), so the
       // three rows' sums over other points are gathered together and the two
       // own-point terms are applied afterwards in C, G, f order.
-      const T aC = row_dot<0, 80, 0, kL>(B, c.cp, j, off, vp, lane, act);
-      const T aG = row_dot<80, 93, 28, kL>(B, c.cp, j, off, vp, lane, act);
-      const T aF = row_dot<94, 174, 70, kL>(B, c.cp, j, off, vp, lane, act);
+      T gC[RowSet<0, 80, kL>::K], gG[RowSet<80, 93, kL>::K], gF[RowSet<94, 174, kL>::K];
+      gather<0, 80, 0, kL>(gC, off, vp, lane, act);
+      gather<80, 93, 28, kL>(gG, off, vp, lane, act);
+      gather<94, 174, 70, kL>(gF, off, vp, lane, act);
+      const T aC = row_sum<0, 80, kL>(gC, B, c.cp, j, lane);
+      const T aG = row_sum<80, 93, kL>(gG, B, c.cp, j, lane);
+      const T aF = row_sum<94, 174, kL>(gF, B, c.cp, j, lane);
       if (act && lane == 0) {
         const T yc = v0 - aC;
         const T yg = v1 - aG - arith<T>(B[93 * c.cp + j]) * yc;
@@ -395,9 +405,13 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
       // Every U-slot reads a point of a later wavefront except the C row's
       // own-f slot (U block row 1), applied after the f row is solved.  The
       // diagonal rows 0, 28, 70 hold the reciprocals of the pivots.
-      const T bF = row_dot<71, 151, 175, kL>(B, c.cp, j, off, vp, lane, act);
-      const T bG = row_dot<29, 70, 94, kL>(B, c.cp, j, off, vp, lane, act);
-      const T bC = row_dot<2, 28, 80, kL>(B, c.cp, j, off, vp, lane, act);
+      T gF[RowSet<71, 151, kL>::K], gG[RowSet<29, 70, kL>::K], gC[RowSet<2, 28, kL>::K];
+      gather<71, 151, 175, kL>(gF, off, vp, lane, act);
+      gather<29, 70, 94, kL>(gG, off, vp, lane, act);
+      gather<2, 28, 80, kL>(gC, off, vp, lane, act);
+      const T bF = row_sum<71, 151, kL>(gF, B, c.cp, j, lane);
+      const T bG = row_sum<29, 70, kL>(gG, B, c.cp, j, lane);
+      const T bC = row_sum<2, 28, kL>(gC, B, c.cp, j, lane);
       if (act && lane == 0) {
         const T zf = (v2 - bF) * arith<T>(B[70 * c.cp + j]);
         const T zg = (v1 - bG) * arith<T>(B[28 * c.cp + j]);
@@ -410,33 +424,17 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL) ras_solve(
     __syncthreads();
     cur = nxt;
     nxt = nn;
-    lex_cur = lex_nxt;
+    vq_cur = vq_nxt;
   };
-  // Forward sweep (unit lower factor), then backward sweep (upper factor).
-  // FP64 runs them as two loops, FP32 as one loop with the direction decided
-  // per step: the faster form of each as measured at 32^3 x 64 (FP64 12.2 ms
-  // vs 28 ms with one loop; FP32 3.7 ms vs 4.2 ms with two).
-  if constexpr (sizeof(T) == 4) {   // FP32 and BF16-stored factors
-    for (int g = 0; g < nblk; ++g) {
-      if (g < nch) step(g, std::false_type{});
-      else step(g, std::true_type{});
-    }
-  } else {
-    for (int g = 0; g < nch; ++g) step(g, std::false_type{});
-    for (int g = nch; g < nblk; ++g) step(g, std::true_type{});
-  }
-  // scatter the owned part: (R^0)^T
-  const int ox = bx.ox1 - bx.ox0, oy = bx.oy1 - bx.oy0, oz = bx.oz1 - bx.oz0, ot = bx.ot1 - bx.ot0;
-  const long long nown = (long long)ox * oy * oz * ot;
-  for (long long q = threadIdx.x; q < nown; q += blockDim.x) {
-    const int gx = bx.ox0 + (int)(q % ox), gy = bx.oy0 + (int)((q / ox) % oy);
-    const int gz = bx.oz0 + (int)((q / ((long long)ox * oy)) % oz), gt = bx.ot0 + (int)(q / ((long long)ox * oy * oz));
-    const int kx = gx - bx.x0, ky = gy - bx.y0, kz = gz - bx.z0, kt = gt - bx.t0;
-    const long long pq = 3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1));
-    const long long g = ((long long)gt * N + gx + (long long)nx * (gy + (long long)ny * gz)) * 3;
-    z[g] = (double)v[pq];
-    z[g + 1] = (double)v[pq + 1];
-    z[g + 2] = (double)v[pq + 2];
+  // forward sweep (unit lower factor), then backward sweep (upper factor)
+  for (int g = 0; g < nch; ++g) step(g, std::false_type{});
+  for (int g = nch; g < nblk; ++g) step(g, std::true_type{});
+  // scatter the owned part: (R^0)^T (otab: the owned points' global indices and offsets)
+  for (int q = threadIdx.x; q < bx.nown; q += blockDim.x) {
+    const int2 e = otab[bx.ooff + q];
+    z[e.x] = (double)v[e.y];
+    z[e.x + 1] = (double)v[e.y + 1];
+    z[e.x + 2] = (double)v[e.y + 2];
   }
 }
 
@@ -621,7 +619,13 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   const int CH = m->ch;
   std::vector<BoxDesc> boxes;
   std::vector<int> perm, iperm, lptr;
-  std::vector<int2> ptab;
+  std::vector<int2> ptab, gtab, otab;
+  std::vector<int> vtab;
+  if (3LL * p->P >= INT32_MAX) {
+    set_error("ras_setup: more than 2^31 unknowns are not supported");
+    delete m;
+    return KKT_ERR_ARG;
+  }
   std::vector<Chunk> chunks;
   long long foff = 0, voff = 0;
   for (int it = 0; it < nsub[3]; ++it)
@@ -667,6 +671,35 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
                 }
           perm.insert(perm.end(), bp.begin(), bp.end());
           iperm.insert(iperm.end(), bi.begin(), bi.end());
+          // index tables of the solve: global index and padded offset of every
+          // point (lexicographic), padded offset in wavefront order, owned points
+          {
+            const long long sy = b.lx + 2, sz = sy * (b.ly + 2), st = sz * (b.lz + 2);
+            auto pad = [&](int kx, int ky, int kz, int kt) {
+              return (int)(3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1)));
+            };
+            auto glob = [&](int kx, int ky, int kz, int kt) {
+              return (int)(3 * ((long long)(b.t0 + kt) * p->N + (b.x0 + kx) +
+                                (long long)p->nx * ((b.y0 + ky) + (long long)p->ny * (b.z0 + kz))));
+            };
+            const size_t g0 = gtab.size();
+            gtab.resize(g0 + b.P);
+            vtab.resize(g0 + b.P);
+            int q = 0;
+            for (int kt = 0; kt < b.lt; ++kt)
+              for (int kz = 0; kz < b.lz; ++kz)
+                for (int ky = 0; ky < b.ly; ++ky)
+                  for (int kx = 0; kx < b.lx; ++kx, ++q) gtab[g0 + q] = make_int2(glob(kx, ky, kz, kt), pad(kx, ky, kz, kt));
+            for (int w = 0; w < (int)b.P; ++w) vtab[g0 + w] = gtab[g0 + bp[w]].y;
+            b.ooff = (long long)otab.size();
+            for (int gt = b.ot0; gt < b.ot1; ++gt)
+              for (int gz = b.oz0; gz < b.oz1; ++gz)
+                for (int gy = b.oy0; gy < b.oy1; ++gy)
+                  for (int gx = b.ox0; gx < b.ox1; ++gx)
+                    otab.push_back(make_int2(glob(gx - b.x0, gy - b.y0, gz - b.z0, gt - b.t0),
+                                             pad(gx - b.x0, gy - b.y0, gz - b.z0, gt - b.t0)));
+            b.nown = (int)((long long)otab.size() - b.ooff);
+          }
           // chunks of each wavefront and the storage offset of every point
           b.cbeg = (int)chunks.size();
           const size_t pt0 = ptab.size();
@@ -746,6 +779,9 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->iperm, iperm.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->lptr, lptr.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->ptab, ptab.size() * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&m->gtab, gtab.size() * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&m->otab, std::max<size_t>(1, otab.size()) * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&m->vtab, vtab.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
       cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * vsz) != cudaSuccess ||
       (factor_prec == 16 && cudaMalloc(&m->Ffac, foff * sizeof(float)) != cudaSuccess) ||
@@ -773,6 +809,10 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   if (e == cudaSuccess) e = cudaMemcpy(m->iperm, iperm.data(), iperm.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->lptr, lptr.data(), lptr.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->ptab, ptab.data(), ptab.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->gtab, gtab.data(), gtab.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !otab.empty())
+    e = cudaMemcpy(m->otab, otab.data(), otab.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->vtab, vtab.data(), vtab.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
   if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * vsz);
@@ -794,18 +834,17 @@ template <typename S, int L>
 kkt_status launch_solve_l(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
                           cudaStream_t s) {
   using T = typename SolveArith<S>::type;
-  const kkt_problem* p = m->prob;
   const int threads = (m->ch * L + 31) / 32 * 32;
   const int bstride = kLRanks * m->cpmax;
   const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(S), sizeof(T), m->max_pad, m->smem_vec);
   if (m->smem_vec) {
     KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, true, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ras_solve<S, true, L><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
-                                                         p->nx, p->ny, p->N, bstride, m->nstage, m->status);
+                                                         m->gtab, m->otab, m->vtab, bstride, m->nstage, m->status);
   } else {
     KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, false, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ras_solve<S, false, L><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
-                                                          p->nx, p->ny, p->N, bstride, m->nstage, m->status);
+                                                          m->gtab, m->otab, m->vtab, bstride, m->nstage, m->status);
   }
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
@@ -934,6 +973,9 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->iperm);
   cudaFree(m->lptr);
   cudaFree(m->ptab);
+  cudaFree(m->gtab);
+  cudaFree(m->otab);
+  cudaFree(m->vtab);
   cudaFree(m->Ffac);
   cudaFree(m->AB);
   cudaFree(m->ipiv);

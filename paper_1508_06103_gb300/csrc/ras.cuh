@@ -31,6 +31,8 @@ struct BoxDesc {
   long long poff;              // offset into perm / iperm
   long long loff;              // offset into the wavefront pointers
   int cbeg, cend;              // chunk range
+  int nown;                    // owned points
+  long long ooff;              // offset into the owned-point table
   int kl;                      // exact LU: half-bandwidth of the box matrix
   long long aoff;              // exact LU: offset of the box's band (elements)
 };
@@ -59,6 +61,9 @@ struct ras_precond {
   int* lptr = nullptr;         // wavefront pointers per box (nlev + 1 each)
   Chunk* chunks = nullptr;
   int nchunk = 0;
+  int2* gtab = nullptr;        // per point (lexicographic): {3 x global point index, padded offset}
+  int2* otab = nullptr;        // per owned point: {3 x global point index, padded offset}
+  int* vtab = nullptr;         // per point (wavefront order): padded offset in the box's local vector
   int2* ptab = nullptr;        // per point (wavefront order): {offset of its column in the box's
                                // chunk blocks, row stride of its block}
   void* F = nullptr;           // factor values (FP64, FP32 or BF16, as the solve reads them)
