@@ -239,6 +239,16 @@ kkt_status ras_refactor(ras_precond* m, void* stream);
 kkt_status coarse_refactor(coarse_level* c, void* stream);
 
 /*
+ * two_level_refactor -- ras_refactor of `fine` and coarse_refactor of `c`
+ *   together: the coarse factorisation runs on a second stream of the library
+ *   (created on the first call) forked from and joined back into `stream`, so
+ *   it can use the SMs the fine one leaves idle.  Synchronises `stream` once;
+ *   errors: ARG (fine is not c's fine level), CUDA, ZERO_PIVOT.  A scheduling
+ *   convenience of this library; the paper has no counterpart.
+ */
+kkt_status two_level_refactor(coarse_level* c, ras_precond* fine, void* stream);
+
+/*
  * Instrumentation (no effect on results).
  * kkt_launch_count  -- number of CUDA kernels the library has launched since it
  *                      was loaded (all handles, all threads).

@@ -49,6 +49,7 @@ SIGNATURES = {
                            C.POINTER(C.c_int)]),
     "ras_solve_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "coarse_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "two_level_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "kkt_launch_count": (C.c_longlong, []),
     "kkt_timing_enable": (C.c_int, [C.c_int]),
     "kkt_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),

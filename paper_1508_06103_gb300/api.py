@@ -182,6 +182,10 @@ class Coarse:
     def refactor(self, stream=None) -> None:
         check(self._lib.coarse_refactor(self.h, _stream(stream)), "coarse_refactor")
 
+    def refactor_with(self, fine: RAS, stream=None) -> None:
+        """Refactor `fine` and this coarse level together (two_level_refactor)."""
+        check(self._lib.two_level_refactor(self.h, fine.h, _stream(stream)), "two_level_refactor")
+
     def close(self):
         if self.h is not None and self.h.value:
             self._lib.coarse_destroy(self.h)

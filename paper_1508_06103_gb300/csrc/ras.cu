@@ -860,20 +860,29 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename Sol
 
 }  // namespace
 
-kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
+kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s) {
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
   if (m->local == 1) KKT_TRY(ras_lu_factor(m, s));
   else if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
   else if (m->prec == 32) KKT_TRY(ras_factor_launch32(m, s));
   else KKT_TRY(ras_factor_launch16(m, s));
+  return KKT_OK;
+}
+
+kkt_status ras_factor_status(ras_precond* m) {
   int st = 0;
-  KKT_TRY_CUDA(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  KKT_TRY_CUDA(cudaStreamSynchronize(s));
+  KKT_TRY_CUDA(cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != 0) {
-    set_error("ras_setup: zero or non-finite pivot in a subdomain ILU(0)");
+    set_error("ras_setup: zero or non-finite pivot in a subdomain factorisation");
     return KKT_ERR_ZERO_PIVOT;
   }
   return KKT_OK;
+}
+
+kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
+  KKT_TRY(ras_factor_enqueue(m, s));
+  KKT_TRY_CUDA(cudaStreamSynchronize(s));
+  return ras_factor_status(m);
 }
 
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s) {

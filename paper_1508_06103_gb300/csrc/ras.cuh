@@ -82,7 +82,9 @@ struct ras_precond {
 
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
                       ras_precond** out);
-kkt_status ras_factor(ras_precond* m, cudaStream_t s);
+kkt_status ras_factor(ras_precond* m, cudaStream_t s);          // enqueue, synchronise, check
+kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s);  // enqueue only
+kkt_status ras_factor_status(ras_precond* m);                   // after the stream completed
 // gather and ILU(0) launches of factor32.cu / factor64.cu
 kkt_status ras_factor_launch32(ras_precond* m, cudaStream_t s);
 kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s);

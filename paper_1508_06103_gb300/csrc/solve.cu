@@ -33,6 +33,8 @@ struct coarse_level {
   float *fx32 = nullptr, *fy32 = nullptr;   // fine FP32 scratch
   GmresWork ws;
   int last_coarse_iters = 0;
+  cudaStream_t aux = nullptr;        // two_level_refactor: stream of the coarse factorisation
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -283,8 +285,34 @@ extern "C" kkt_status coarse_refactor(coarse_level* c, void* stream) {
   return ras_factor(c->cras, (cudaStream_t)stream);
 }
 
+extern "C" kkt_status two_level_refactor(coarse_level* c, ras_precond* fine, void* stream) {
+  if (!c || !fine || fine->prob != c->fine) {
+    set_error("two_level_refactor: bad argument");
+    return KKT_ERR_ARG;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (!c->aux) {
+    KKT_TRY_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    KKT_TRY_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    KKT_TRY_CUDA(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+  }
+  // the coarse factorisation fills the SMs the fine one leaves idle
+  KKT_TRY_CUDA(cudaEventRecord(c->fork, s));
+  KKT_TRY_CUDA(cudaStreamWaitEvent(c->aux, c->fork, 0));
+  KKT_TRY(ras_factor_enqueue(fine, s));
+  KKT_TRY(ras_factor_enqueue(c->cras, c->aux));
+  KKT_TRY_CUDA(cudaEventRecord(c->join, c->aux));
+  KKT_TRY_CUDA(cudaStreamWaitEvent(s, c->join, 0));
+  KKT_TRY_CUDA(cudaStreamSynchronize(s));
+  KKT_TRY(ras_factor_status(fine));
+  return ras_factor_status(c->cras);
+}
+
 extern "C" void coarse_destroy(coarse_level* c) {
   if (!c) return;
+  if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
   ras_destroy(c->cras);
   kkt_destroy(c->cp);
   cudaFree(c->rc);

@@ -151,6 +151,24 @@ def test_two_level_apply_fp64_matches_oracle(api):
     assert np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
 
 
+def test_two_level_refactor_equals_separate_refactors(api):
+    # the combined call runs the same factorisations, only on two streams
+    w = _two_level_case()
+    prob = api.Problem.from_workload(w)
+    x = _dev(W.random_vector(prob.n, 7))
+    outs = []
+    for together in (False, True):
+        ras = api.RAS(prob, w.nsub, w.overlap, 32)
+        coarse = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, 1, 0.1, 4, 32)
+        if together:
+            coarse.refactor_with(ras)
+        else:
+            ras.refactor()
+            coarse.refactor()
+        outs.append(coarse.apply(ras, x).cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
 def _exact(w):
     p = okkt.Problem.from_workload(w)
     F = okkt.assemble(p)
