@@ -233,6 +233,17 @@ def reference_arm(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
+    """The largest value over the ranks of the process group (the job's time)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -295,12 +306,7 @@ def gpu_arm(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dist, "cuda")
 
     # ---- mixed form: the headline -----------------------------------------
     ras, co = make(32)

@@ -186,16 +186,19 @@ __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T
     const T mt0 = (hasm ? tau / (T)3 : (T)0) + (hasp ? tau / (T)3 : (T)0);
     const T ltm = hasm ? -(T)1 / tau : (T)0, ltp = hasp ? -(T)1 / tau : (T)0;
     const T lt0 = (hasm ? (T)1 / tau : (T)0) + (hasp ? (T)1 / tau : (T)0);
+    // the weights of the six combinations, formed once per level
+    const T wt0 = tau * th, wt1 = tau * th1;
+    const T lm = b1 * ltm, l0 = b1 * lt0, lp = b1 * ltp, km = b2 * mtm, k0 = b2 * mt0, kp = b2 * mtp;
     for (int h = t; h < NH; h += blockDim.x) {
       const T Cm = Xm[h], Gm = Xm[NH + h], Fm = Xm[2 * NH + h];
       const T C0 = X0[h], G0 = X0[NH + h], F0 = X0[2 * NH + h];
       const T Gp = Xp[NH + h], Fp = Xp[2 * NH + h];
-      U[h] = (C0 - Cm) - tau * (th * F0 + th1 * Fm);
-      U[NH + h] = tau * (th * C0 + th1 * Cm);
+      U[h] = (C0 - Cm) - (wt0 * F0 + wt1 * Fm);
+      U[NH + h] = wt0 * C0 + wt1 * Cm;
       U[2 * NH + h] = G0 - Gp;
-      U[3 * NH + h] = tau * (th * G0 + th1 * Gp);
-      U[4 * NH + h] = -(mtm * Gm + mt0 * G0 + mtp * Gp) + b1 * (ltm * Fm + lt0 * F0 + ltp * Fp);
-      U[5 * NH + h] = b2 * (mtm * Fm + mt0 * F0 + mtp * Fp);
+      U[3 * NH + h] = wt0 * G0 + wt1 * Gp;
+      U[4 * NH + h] = (lm * Fm + l0 * F0 + lp * Fp) - (mtm * Gm + mt0 * G0 + mtp * Gp);
+      U[5 * NH + h] = km * Fm + k0 * F0 + kp * Fp;
     }
     __syncthreads();
     if (n + 3 <= n1) prefetch(n + 3);    // into the slot of level n - 1, no longer read

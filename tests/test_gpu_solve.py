@@ -102,6 +102,16 @@ def test_exact_lu_rejects_other_precisions_and_static_apply(api):
         ras.apply_static(_dev(W.random_vector(prob.n, 1)))
 
 
+def test_solve_shape_is_reported_and_valid(api):
+    # the chunk size, copy-ring depth and vector placement chosen at set-up
+    case = RAS_CASES[1]
+    w = W.random_small(nsens=6, **case["w"])
+    prob = api.Problem.from_workload(w)
+    for prec, sizes in ((64, {32, 20, 12}), (32, {56, 40, 24, 28, 20, 12}), (16, {80, 48, 16})):
+        sh = api.RAS(prob, case["nsub"], case["ov"], prec).solve_shape()
+        assert sh["chunk_points"] in sizes and 2 <= sh["stages"] <= 4 and isinstance(sh["smem_vectors"], bool)
+
+
 def test_ras_apply_fp32_close_to_oracle(api):
     case = RAS_CASES[0]
     w = W.random_small(nsens=6, **case["w"])
