@@ -25,7 +25,11 @@ namespace {
 #include "ilu_rows.inc"
 
 constexpr int kGatherThreads = 256;
-constexpr int kFactorThreads = 128;   // two CTAs per SM: all 256 boxes resident at once
+// Threads per factor CTA, two CTAs per SM (all 256 boxes of the 4x4x4x4
+// partition resident at once).  FP32 rows fit 192 threads without large
+// spills; FP64 rows need the registers of 128.
+template <typename T>
+constexpr int factor_threads = sizeof(T) == 4 ? 192 : 128;
 
 // One thread per point (wavefront order, so the threads of a chunk write
 // consecutive addresses); all threads of a warp on the same slot.  Entries are
@@ -56,14 +60,15 @@ __device__ __forceinline__ void check_pivot(double d, int* status) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFactorThreads, 2) ilu0_factor(const BoxDesc* __restrict__ boxes,
+__global__ void __launch_bounds__(factor_threads<T>, 2) ilu0_factor(const BoxDesc* __restrict__ boxes,
                                                                  const int* __restrict__ iperm,
                                                                  const int* __restrict__ perm,
                                                                  const int* __restrict__ lptr,
                                                                  const int2* __restrict__ ptab, T* __restrict__ F,
                                                                  int* __restrict__ status) {
   // per thread and pivot point: {offset of its column in Fb, row stride of its block}
-  __shared__ int2 nbs[kGenNbrs * kFactorThreads];
+  constexpr int NS = factor_threads<T>;
+  __shared__ int2 nbs[kGenNbrs * NS];
   const BoxDesc bx = boxes[blockIdx.x];
   T* Fb = F + bx.foff;
   const int* lp = lptr + bx.loff;
@@ -85,12 +90,11 @@ __global__ void __launch_bounds__(kFactorThreads, 2) ilu0_factor(const BoxDesc* 
         int2 e = make_int2(unit, 1);
         if (ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz && at >= 0 && at < bx.lt)
           e = pb[ip[ax + bx.lx * (ay + bx.ly * (az + bx.lz * at))]];
-        nb[i * kFactorThreads] = e;
+        nb[i * NS] = e;
       }
       const int2 pt = pb[q];
       T* own = Fb + pt.x;
       // the G and f rows read the U parts of this point's C and G rows
-      constexpr int NS = kFactorThreads;
       if constexpr (sizeof(T) == 4) {
         check_pivot((double)ilu_row0_32<T, NS>(own, pt.y, Fb, nb), status);
         asm volatile("" ::: "memory");
@@ -121,7 +125,7 @@ kkt_status factor_launch(ras_precond* m, T* F, cudaStream_t s) {
   KKT_TRY_CUDA(cudaGetLastError());
   {
     TimedScope timed(&m->factor_timing, s);
-    ilu0_factor<T><<<m->nbox, kFactorThreads, 0, s>>>(m->boxes, m->iperm, m->perm, m->lptr, m->ptab, F,
+    ilu0_factor<T><<<m->nbox, factor_threads<T>, 0, s>>>(m->boxes, m->iperm, m->perm, m->lptr, m->ptab, F,
                                                       m->status);
   }
   KKT_COUNT(1);
