@@ -6,7 +6,8 @@
 // Values.  gather_chunks forms every slot value of every box point from the
 // stencil coefficients (the principal submatrix of F_h on the extended box,
 // Eq. 10-12; a slot whose column leaves the box holds 0) and writes it to the
-// point's column of its chunk block, row c_gen_rank[slot].
+// point's column of its chunk block, row c_gen_rank[slot] (c_gen_rank_of by
+// the slot's offsets).
 //
 // Elimination.  One CTA per box steps through the wavefronts
 // w = x + 2y + 4z + 8t with a barrier between them; one thread takes one point
@@ -33,7 +34,12 @@ constexpr int factor_threads = sizeof(T) == 4 ? 192 : 128;
 
 // One thread per point (wavefront order, so the threads of a chunk write
 // consecutive addresses); all threads of a warp on the same slot.  Entries are
-// formed in the factor precision.  Also writes each box's unit row.
+// formed in the factor precision, with the arithmetic of slot_value, but one
+// spatial offset at a time: the point's B, S, S^T and K coefficients of that
+// offset are loaded once and give all 12 slots that share it (C row: C and f
+// columns at levels n-1, n; G row: G column at n, n+1; f row: G and f columns
+// at n-1, n, n+1), plus the G row's two sensor slots at the centre.  Also
+// writes each box's unit row.
 template <typename T>
 __global__ void __launch_bounds__(kGatherThreads) gather_chunks(DevProblem p, const BoxDesc* __restrict__ boxes,
                                                                 const int* __restrict__ perm,
@@ -49,10 +55,49 @@ __global__ void __launch_bounds__(kGatherThreads) gather_chunks(DevProblem p, co
   const PointRow<T> pr = point_row<T>(p, bx, perm[bx.poff + q]);
   const int2 pt = ptab[bx.poff + q];
   T* dst = Fb + pt.x;
-  for (int s = 0; s < kSlots; ++s) {
-    bool inb;
-    dst[(long long)c_gen_rank[s] * pt.y] = slot_value<T>(p, bx, cf, pr, s, &inb);
+  const long long st = pt.y;
+  const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta), b1 = (T)p.beta1, b2 = (T)p.beta2;
+  const T mt1 = tau / (T)6, lt1 = -(T)1 / tau;
+  const bool idC = pr.n == 0 || pr.dirj, idG = pr.n == p.M || pr.dirj;   // identity rows
+  const bool tm = pr.kt > 0, tp = pr.kt + 1 < bx.lt;                      // levels n-1, n+1 in the box
+  const T z = (T)0;
+  // slot (row type c, level offset dt, spatial offset d, column component cc)
+#define PUT(c, dt, d, cc, v) dst[(long long)c_gen_rank_of[c][(dt) + 1][d][cc] * st] = (v)
+#pragma unroll
+  for (int d = 0; d < kStencil; ++d) {
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    const int ax = pr.kx + dx, ay = pr.ky + dy, az = pr.kz + dz;
+    const bool sp = ax >= 0 && ax < bx.lx && ay >= 0 && ay < bx.ly && az >= 0 && az < bx.lz;
+    T Bv = z, Sv = z, STv = z, Kv = z;
+    if (sp) {
+      const size_t ci = (size_t)d * p.N + pr.j;
+      Bv = cf.B[ci];
+      Sv = cf.S[ci];
+      STv = cf.ST[ci];
+      Kv = cf.K[ci];
+    }
+    constexpr int kCentre = 13;
+    // C row
+    PUT(0, 0, d, 0, !sp ? z : idC ? (d == kCentre ? (T)1 : z) : Bv + th * tau * Sv);
+    PUT(0, 0, d, 2, !sp || idC ? z : -th * tau * Bv);
+    PUT(0, -1, d, 0, !sp || !tm || idC ? z : -Bv + th1 * tau * Sv);
+    PUT(0, -1, d, 2, !sp || !tm || idC ? z : -th1 * tau * Bv);
+    // G row
+    PUT(1, 0, d, 1, !sp ? z : idG ? (d == kCentre ? (T)1 : z) : Bv + th * tau * STv);
+    PUT(1, 1, d, 1, !sp || !tp || idG ? z : -Bv + th1 * tau * STv);
+    if (d == kCentre) {
+      PUT(1, 0, d, 0, idG ? z : th1 * tau * pr.sj);
+      PUT(1, 1, d, 0, !tp || idG ? z : th * tau * pr.sj);
+    }
+    // f row
+    PUT(2, -1, d, 1, !sp || !tm ? z : -mt1 * Bv);
+    PUT(2, -1, d, 2, !sp || !tm ? z : b1 * lt1 * Bv + b2 * mt1 * Kv);
+    PUT(2, 0, d, 1, !sp ? z : -pr.mt0 * Bv);
+    PUT(2, 0, d, 2, !sp ? z : b1 * pr.lt0 * Bv + b2 * pr.mt0 * Kv);
+    PUT(2, 1, d, 1, !sp || !tp ? z : -mt1 * Bv);
+    PUT(2, 1, d, 2, !sp || !tp ? z : b1 * lt1 * Bv + b2 * mt1 * Kv);
   }
+#undef PUT
 }
 
 __device__ __forceinline__ void check_pivot(double d, int* status) {

@@ -1,6 +1,7 @@
 """Generate ilu_rows.inc: straight-line ILU(0) elimination of one KKT row per thread.
 
-(and ilu_slots.inc: the slot list's checksum and each slot's row in a chunk block)
+(and ilu_slots.inc: the slot list's checksum and each slot's row in a chunk block,
+also indexed by the slot's offsets for the value gather)
 
 Every row of the space-time KKT matrix is one of three types (C, G, f) with
 a fixed structural stencil of slots (level offset dt, spatial offset, column
@@ -177,6 +178,22 @@ def generate() -> str:
     hdr.append("__constant__ short c_gen_rank[%d] = {" % len(slots))
     for a in range(0, len(slots), 20):
         hdr.append("    " + ", ".join(str(r) for r in rank[a:a + 20]) + ",")
+    hdr.append("};")
+    # inverse table: rank of the slot (row type, dt + 1, spatial offset, column component)
+    rank_of = [[[[-1] * 3 for _ in range(27)] for _ in range(3)] for _ in range(3)]
+    for c in range(3):
+        for s in range(base[c], base[c] + count[c]):
+            dt, dz, dy, dx, cc = slots[s]
+            rank_of[c][dt + 1][(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)][cc] = rank[s]
+    hdr.append("// rank of the slot of row type c with level offset dt, spatial offset")
+    hdr.append("// d = (dx+1) + 3 (dy+1) + 9 (dz+1) and column component cc, at [c][dt+1][d][cc];")
+    hdr.append("// -1 where the row type has no such slot")
+    hdr.append("__constant__ short c_gen_rank_of[3][3][27][3] = {")
+    for c in range(3):
+        hdr.append("    {")
+        for t in range(3):
+            hdr.append("        {" + ", ".join("{%d, %d, %d}" % tuple(v) for v in rank_of[c][t]) + "},")
+        hdr.append("    },")
     hdr.append("};")
     hdr.append("#endif")
     hdr.append("")

@@ -69,13 +69,13 @@ constexpr size_t mv_smem() {
 
 // 1D linear-element mass and stiffness rows on one axis of n nodes with
 // width h: row i has (i > 0) + (i < n - 1) elements; the entries are chosen
-// from values formed once per thread (no arithmetic per node).
+// from values formed once on the host (no arithmetic per node).
 template <typename T>
 struct Axis1D {
   int n;
   T m1, m2, mo, k1, k2, ko;   // mass diagonal (one / two elements), off-diagonal; the same for stiffness
   T hh;                       // the width
-  __device__ __forceinline__ void init(int n_, double h) {
+  __host__ __device__ void init(int n_, double h) {
     n = n_;
     m1 = (T)(h / 3.0);
     m2 = (T)(2.0 * h / 3.0);
@@ -106,6 +106,34 @@ struct Axis1D {
   }
 };
 
+// Weights of the six time combinations: the theta weights and the rows of
+// the 1D linear-element time mass Mt (tau/6 [1 4 1]) and stiffness Lt
+// ([-1 2 -1]/tau) scaled by beta1 and beta2.  A level has one time element
+// on each side it has a neighbour; the diagonal entries for one and two
+// elements are formed on the host, in T, so a level only selects.
+template <typename T>
+struct LevelW {
+  T wt0, wt1;          // tau theta, tau (1 - theta)
+  T mto, mtd1, mtd2;   // Mt: off-diagonal; diagonal with one, two elements
+  T lo, ld1, ld2;      // beta1 Lt
+  T ko, kd1, kd2;      // beta2 Mt
+  void init(double tau_, double theta, double beta1, double beta2) {
+    const T tau = (T)tau_, th = (T)theta, th1 = (T)(1.0 - theta), b1 = (T)beta1, b2 = (T)beta2;
+    const T m6 = tau / (T)6, m3 = tau / (T)3, l1 = (T)1 / tau;
+    wt0 = tau * th;
+    wt1 = tau * th1;
+    mto = m6;
+    mtd1 = m3;
+    mtd2 = m3 + m3;
+    lo = b1 * -l1;
+    ld1 = b1 * l1;
+    ld2 = b1 * (l1 + l1);
+    ko = b2 * m6;
+    kd1 = b2 * m3;
+    kd2 = b2 * (m3 + m3);
+  }
+};
+
 // asynchronous global -> shared copy of one value; zero-filled when !valid
 template <typename T>
 __device__ __forceinline__ void cp_async_value(T* dst, const T* src, bool valid) {
@@ -124,7 +152,8 @@ __device__ __forceinline__ void cp_async_wait() {
 template <typename T>
 __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T* __restrict__ x,
                                                            T* __restrict__ y, const double* __restrict__ b,
-                                                           int tiles_x, int tiles_y) {
+                                                           int tiles_x, int tiles_y, Axis1D<T> ax, Axis1D<T> ay,
+                                                           Axis1D<T> az, LevelW<T> W) {
   extern __shared__ __align__(16) unsigned char mv_sm[];
   T* Xs = reinterpret_cast<T*>(mv_sm);   // [4 slots][3 components][NH]
   T* U = Xs + 4 * 3 * NH;                // [6][NH]
@@ -136,11 +165,6 @@ __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T
   const int n0 = blockIdx.y * NT, n1 = min(n0 + NT, M + 1);
   const Coefs<T> c = coefs<T>(p);
   const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta);
-  const T b1 = (T)p.beta1, b2 = (T)p.beta2;
-  Axis1D<T> ax, ay, az;
-  ax.init(p.nx, p.hx);
-  ay.init(p.ny, p.hy);
-  az.init(p.nz, p.hz);
   const int t = threadIdx.x;
   const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
   const int ix = bx0 + tx, iy = by0 + ty, iz = bz0 + tz;
@@ -182,13 +206,14 @@ __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T
     const T* X0 = Xs + (size_t)(n % 4) * 3 * NH;
     const T* Xp = Xs + (size_t)((n + 1) % 4) * 3 * NH;
     const bool hasm = n > 0, hasp = n < M;
-    const T mtm = hasm ? tau / (T)6 : (T)0, mtp = hasp ? tau / (T)6 : (T)0;
-    const T mt0 = (hasm ? tau / (T)3 : (T)0) + (hasp ? tau / (T)3 : (T)0);
-    const T ltm = hasm ? -(T)1 / tau : (T)0, ltp = hasp ? -(T)1 / tau : (T)0;
-    const T lt0 = (hasm ? (T)1 / tau : (T)0) + (hasp ? (T)1 / tau : (T)0);
-    // the weights of the six combinations, formed once per level
-    const T wt0 = tau * th, wt1 = tau * th1;
-    const T lm = b1 * ltm, l0 = b1 * lt0, lp = b1 * ltp, km = b2 * mtm, k0 = b2 * mt0, kp = b2 * mtp;
+    // the weights of the six combinations at this level
+    const T wt0 = W.wt0, wt1 = W.wt1;
+    const T mtm = hasm ? W.mto : (T)0, mtp = hasp ? W.mto : (T)0;
+    const T lm = hasm ? W.lo : (T)0, lp = hasp ? W.lo : (T)0;
+    const T km = hasm ? W.ko : (T)0, kp = hasp ? W.ko : (T)0;
+    const T mt0 = hasm && hasp ? W.mtd2 : (hasm || hasp ? W.mtd1 : (T)0);
+    const T l0 = hasm && hasp ? W.ld2 : (hasm || hasp ? W.ld1 : (T)0);
+    const T k0 = hasm && hasp ? W.kd2 : (hasm || hasp ? W.kd1 : (T)0);
     for (int h = t; h < NH; h += blockDim.x) {
       const T Cm = Xm[h], Gm = Xm[NH + h], Fm = Xm[2 * NH + h];
       const T C0 = X0[h], G0 = X0[NH + h], F0 = X0[2 * NH + h];
@@ -279,8 +304,14 @@ template <typename T>
 void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
   const int tx = (p.nx + TX - 1) / TX, ty = (p.ny + TY - 1) / TY, tz = (p.nz + TZ - 1) / TZ;
   dim3 grid(tx * ty * tz, (p.M + 1 + NT - 1) / NT);
+  Axis1D<T> ax, ay, az;
+  ax.init(p.nx, p.hx);
+  ay.init(p.ny, p.hy);
+  az.init(p.nz, p.hz);
+  LevelW<T> w;
+  w.init(p.tau, p.theta, p.beta1, p.beta2);
   cudaFuncSetAttribute(matvec_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T>());
-  matvec_tiled<T><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty);
+  matvec_tiled<T><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
 }
 
 __global__ void d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {

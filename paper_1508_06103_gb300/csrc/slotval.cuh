@@ -1,9 +1,11 @@
 // Values of the subdomain matrices M_ij = R^delta F_h (R^delta)^T (Eq. 10-12),
 // slot by slot: the principal submatrix of F_h on an extended box, so a slot
-// whose column leaves the box is 0.  Shared by the ILU(0) factorisation
-// (factor.cuh) and the exact banded LU (lu.cu).  Entries are formed in the
-// precision T of the factorisation from the stencil coefficients of
-// problem.cu (the Appendix block rows with the theta scheme).
+// whose column leaves the box is 0.  The exact banded LU (lu.cu) gathers
+// with slot_value; the ILU(0) gather (factor.cuh) uses the per-point
+// constants and forms the same values one spatial offset at a time.
+// Entries are formed in the precision T of the factorisation from the
+// stencil coefficients of problem.cu (the Appendix block rows with the theta
+// scheme).
 #pragma once
 
 #include "internal.cuh"
