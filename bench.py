@@ -500,6 +500,72 @@ def kernel_arm(args):
     print(json.dumps(out))
 
 
+def sweep_arm(args):
+    """Overlap and level sweep of the mixed-form solve at 32^3 x 64 (the trends of the paper's
+    Tables 2 and 3: iterations and time against the overlap, one level against two).
+
+    For each preconditioner: fine FP32 factors with overlap delta (the coarse level as in the
+    workload), one refactorisation and one solve untimed, then the refactorisation and
+    `--reps` solves timed with CUDA events, SM clocks sampled meanwhile.  One JSON line per
+    preconditioner, the workload's own (two levels, overlap 2) first.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    build.build()
+    w = W.mid()
+    cobs = torch.from_numpy(np.loadtxt(OBS_FILE, ndmin=2)).cuda()
+    prob = api.Problem.from_workload(w)
+    b, x = prob.zeros(), prob.zeros()
+    prob.rhs(cobs, out=b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for levels, delta in ((2, 2), (2, 0), (2, 1), (2, 3), (1, 1), (1, 2)):
+        ras = api.RAS(prob, w.nsub, delta, 32)
+        co = None
+        if levels == 2:
+            co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, w.coarse_overlap, w.coarse_rtol,
+                            w.coarse_maxit, 32)
+        last = {}
+
+        def refactor():
+            if co is not None:
+                co.refactor_with(ras)
+            else:
+                ras.refactor()
+
+        def solve():
+            x.zero_()
+            _, st, its, rel = api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=w.restart, rtol=w.rtol,
+                                              maxit=3000)
+            last.update(status=st, iterations=its, relres=rel)
+
+        refactor()
+        solve()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            out = {"levels": levels, "overlap": delta, "refactor_ms": timed(refactor, 1),
+                   "solve_ms": timed(solve, args.reps)}
+        out.update(last)
+        out["clocks"] = clk.summary()
+        out["box_points"] = ras.info()["points"]
+        print(json.dumps(out), flush=True)
+        if co is not None:
+            co.close()
+        ras.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,14 +574,17 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["ras", "matvec"], default=None,
-                    help="time one kernel on a member of the workload family instead of the full solve")
+    ap.add_argument("--kernel", choices=["ras", "matvec", "sweep"], default=None,
+                    help="time one kernel on a member of the workload family instead of the full solve; "
+                         "sweep: overlap and one/two-level sweep of the mixed-form solve")
     ap.add_argument("--cells", type=int, default=32)
     ap.add_argument("--levels", type=int, default=64)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--prec", type=int, default=32)
     args = ap.parse_args()
-    if args.kernel:
+    if args.kernel == "sweep":
+        sweep_arm(args)
+    elif args.kernel:
         kernel_arm(args)
     elif args.impl == "reference":
         reference_arm(args)
