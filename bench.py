@@ -375,7 +375,7 @@ def gpu_arm(args):
 
     peak, peak_kind = measured_peaks()
     traffic = {k: read_traffic(k) for k in ("ras_solve", "ilu0_factor", "matvec_tiled")}
-    # algorithmic bytes per launch (unpadded values)
+    # algorithmic bytes per launch (unpadded values: no chunk padding or unit rows counted)
     vb = info["value_bytes"]
     fvals = info["points"] * SLOTS_PER_POINT
     kernels = {
@@ -383,7 +383,7 @@ def gpu_arm(args):
                             ms=fac_ms, n=fac_n, bytes=2 * fvals * vb),
         "ras_solve": dict(desc="fine subdomain ILU(0) solve, all 256 boxes, FP32 factors",
                           ms=ras_ms, n=ras_n, bytes=fvals * vb + info["points"] * 3 * 8 + prob.n * 8),
-        "matvec_tiled": dict(desc="outer FP64 KKT matvec (FP64-pipe bound, see DESIGN.md)",
+        "matvec_tiled": dict(desc="outer FP64 KKT matvec (bound by the FP64 pipe, not by HBM)",
                              ms=mv_ms, n=mv_n, bytes=mv64_bytes),
     }
     table = {}

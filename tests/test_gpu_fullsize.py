@@ -5,7 +5,7 @@
   solution, which must be <= 1e-8 (the stop test) in the FP64 form and the
   mixed form with FP32 or BF16-stored factors; the recovered sources of the
   mixed forms, solved to 1e-10, agree with the FP64 form's to 1e-5 relative
-  L2 (the benchmark spec's bound for the mixed form).
+  L2 (the accuracy bound stated for the mixed form).
 * 8^3 cells x 16 implicit-Euler steps (37,179 unknowns), one-level RAS
   2x2x2x2, overlap 1, exact local LU (and ILU(0)): the GPU solution agrees
   with the oracle's solution of the same system to 1e-8 relative after both

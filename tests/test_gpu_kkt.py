@@ -1,7 +1,7 @@
 """GPU parity of the KKT matvec, right-hand side and source extraction against the oracle.
 
 Tolerances (derived from the arithmetic):
-* FP64 matvec: spec bound 1e-12, applied per output as
+* FP64 matvec: the stated bound 1e-12, applied per output as
   |y_gpu - y_ref| <= 1e-12 (|F| |x|)_i  -- each output is a sum of at most
   ~330 products, so the rounding of either side is below 330 u (|F||x|)_i
   with u = 1.1e-16, i.e. < 4e-14 (|F||x|)_i.

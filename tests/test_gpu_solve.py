@@ -11,7 +11,7 @@ Tolerances:
   The check is max|dz| <= 1e-9 max|z|.
 * two-level apply, FP64: also runs the 4-step coarse GMRES (CGS2) on both
   sides; same bound.
-* FP64 solve: the benchmark spec's bound, relative 2-norm error of U <= 1e-8
+* FP64 solve: the stated bound, relative 2-norm error of U <= 1e-8
   against the oracle's sparse direct solve, after solving to rtol 1e-13 (the
   KKT matrix is ill-conditioned, so a 1e-8 residual alone does not give a
   1e-8 error).
