@@ -23,6 +23,11 @@ permuted to the point-block order.  With a time-stepping weight theta
   f rows, n = 0..M     : sum_m (-D^{nm} G^m + W^{nm} f^m)             = 0
       D^{nm} = Mt[n,m] B,  W^{nm} = beta1 Lt[n,m] B + beta2 Mt[n,m] K
 
+K is the stiffness matrix of the H1-H1 regularisation N_beta (Eq. 3, the
+(grad f, grad g) term of Eq. 9); the H1-L2 regularisation of Sec. 4
+(Example 2) replaces |grad f|^2 by f^2, so K becomes the mass matrix B
+there (reg = "h1l2").
+
 B3 = diag(s), s_j = number of sensors snapped to node j.  On Dirichlet nodes
 (Gamma_1) the C and G rows are identity rows (the columns are kept), with
 right-hand side p = 0 (all workloads use homogeneous Dirichlet data); the
@@ -45,7 +50,7 @@ class Problem:
     """Discrete data of one inverse problem (everything the KKT needs)."""
 
     def __init__(self, cells, lengths, T, M, theta, dirichlet_faces, a_cell, v_cell,
-                 sensor_node, beta1, beta2):
+                 sensor_node, beta1, beta2, reg="h1h1"):
         self.cells = tuple(int(c) for c in cells)
         self.lengths = tuple(float(l) for l in lengths)
         self.nodes = tuple(c + 1 for c in self.cells)
@@ -61,7 +66,12 @@ class Problem:
         self.sensor_node = np.asarray(sensor_node, dtype=np.int64)
         self.beta1 = float(beta1)
         self.beta2 = float(beta2)
+        if reg not in ("h1h1", "h1l2"):
+            raise ValueError("reg must be 'h1h1' or 'h1l2'")
+        self.reg = reg
         self.B, self.A, self.Es, self.K = fem.spatial_matrices(self.cells, self.lengths, self.a_cell, self.v_cell)
+        # spatial matrix of the beta2 term: stiffness (H1-H1) or mass (H1-L2)
+        self.W2 = self.K if reg == "h1h1" else self.B
         self.S = (self.A + self.Es).tocsr()
         self.Mt, self.Lt = fem.time_matrices(self.M, self.tau)
         self.dirichlet = fem.dirichlet_mask(self.cells, self.faces)
@@ -74,7 +84,7 @@ class Problem:
     @classmethod
     def from_workload(cls, w):
         return cls(w.cells, w.lengths, w.T, w.M, w.theta, w.dirichlet_faces, w.a_cell,
-                   w.v_cell, w.sensor_nodes(), w.beta1, w.beta2)
+                   w.v_cell, w.sensor_nodes(), w.beta1, w.beta2, getattr(w, "reg", "h1h1"))
 
     # index helpers ------------------------------------------------------
     def pb_index(self, n, j, c):
@@ -122,7 +132,7 @@ def assemble_field_major(p: Problem, nodes=None, levels=None) -> sp.csr_matrix:
     N, L = len(nodes), len(levels)
     sub = lambda A: A[nodes][:, nodes].tocsr()
     A1, A2, B1, B2 = (sub(X) for X in _state_blocks(p))
-    Bs, Ks = sub(p.B), sub(p.K)
+    Bs, Ws = sub(p.B), sub(p.W2)
     I = sp.identity(N, format="csr")
     Z = None
     D = p.dirichlet[nodes]
@@ -161,7 +171,7 @@ def assemble_field_major(p: Problem, nodes=None, levels=None) -> sp.csr_matrix:
         r = 2 * L + k
         for m in range(max(0, n - 1), min(M, n + 1) + 1):
             put(r, 1, m, -Mt[n, m] * Bs)
-            put(r, 2, m, p.beta1 * Lt[n, m] * Bs + p.beta2 * Mt[n, m] * Ks)
+            put(r, 2, m, p.beta1 * Lt[n, m] * Bs + p.beta2 * Mt[n, m] * Ws)
     # every block row and column needs a defined shape for bmat
     for r in range(3 * L):
         if blocks[r][r] is None:
@@ -233,7 +243,7 @@ def apply(p: Problem, U: np.ndarray) -> np.ndarray:
     for n in range(M + 1):
         acc = np.zeros(N)
         for m in range(max(0, n - 1), min(M, n + 1) + 1):
-            acc += -Mt[n, m] * (p.B @ G[m]) + p.beta1 * Lt[n, m] * (p.B @ f[m]) + p.beta2 * Mt[n, m] * (p.K @ f[m])
+            acc += -Mt[n, m] * (p.B @ G[m]) + p.beta1 * Lt[n, m] * (p.B @ f[m]) + p.beta2 * Mt[n, m] * (p.W2 @ f[m])
         Y[n, :, 2] = acc
     return Y.reshape(-1)
 

@@ -71,6 +71,8 @@ class Workload:
     coarse_maxit: int = 4
     restart: int = 30
     rtol: float = 1e-8
+    # regularisation: "h1h1" (N_beta, Eq. 3) or "h1l2" (beta2 |grad f|^2 -> beta2 f^2, Sec. 4 Example 2)
+    reg: str = "h1h1"
 
     # ---- derived sizes -------------------------------------------------
     @property
@@ -193,7 +195,7 @@ def switching(windows: Sequence[Tuple[float, float]]):
 # the workloads
 # ---------------------------------------------------------------------------
 
-def tiny(theta: float = 1.0) -> Workload:
+def tiny(theta: float = 1.0, reg: str = "h1h1") -> Workload:
     """8^3 cells x 16 implicit-Euler steps, one source moving on a line, 27 sensors."""
     cells, L = (8, 8, 8), (1.0, 1.0, 1.0)
     ncell = 8 ** 3
@@ -205,7 +207,7 @@ def tiny(theta: float = 1.0) -> Workload:
         sensor_xyz=sensor_lattice(3, L), beta1=beta / 100, beta2=beta,
         sources=[Source(center=linear_path((0.3, 0.3, 0.5), (0.7, 0.7, 0.5), 1.0))],
         noise_eps=0.01, noise_seed=1,
-        nsub=(2, 2, 2, 2), overlap=1, local="lu", restart=30, rtol=1e-8,
+        nsub=(2, 2, 2, 2), overlap=1, local="lu", restart=30, rtol=1e-8, reg=reg,
     )
 
 
@@ -259,7 +261,7 @@ def large() -> Workload:
 
 
 def random_small(seed: int, cells=(5, 4, 3), M: int = 5, theta: float = 0.5,
-                 dirichlet_faces: int = FACE_X0 | FACE_Y1, nsens: int = 6) -> Workload:
+                 dirichlet_faces: int = FACE_X0 | FACE_Y1, nsens: int = 6, reg: str = "h1h1") -> Workload:
     """Small problem with random coefficients, for parity tests on ragged sizes."""
     rng = np.random.Generator(np.random.PCG64(seed))
     L = (1.0, 0.8, 0.6)
@@ -271,7 +273,7 @@ def random_small(seed: int, cells=(5, 4, 3), M: int = 5, theta: float = 0.5,
         name=f"random_{seed}", cells=tuple(cells), lengths=L, T=1.0, M=M, theta=theta,
         dirichlet_faces=dirichlet_faces, a_cell=a, v_cell=v, sensor_xyz=xyz,
         beta1=1e-4, beta2=1e-2, sources=[Source(center=lambda t: (0.5, 0.4, 0.3))],
-        noise_eps=0.0, noise_seed=seed,
+        noise_eps=0.0, noise_seed=seed, reg=reg,
     )
 
 

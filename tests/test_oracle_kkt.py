@@ -13,10 +13,11 @@ from paper_1508_06103_gb300 import workloads as W
 PI = math.pi
 
 
-def _cube_problem(c, M, theta=0.5, a=0.2, v=(0.3, -0.2, 0.1), faces=W.ALL_FACES, sensors=(), beta=(1e-3, 1e-2)):
+def _cube_problem(c, M, theta=0.5, a=0.2, v=(0.3, -0.2, 0.1), faces=W.ALL_FACES, sensors=(), beta=(1e-3, 1e-2),
+                  reg="h1h1"):
     ncell = c ** 3
     return kkt.Problem((c, c, c), (1.0, 1.0, 1.0), 1.0, M, theta, faces, np.full(ncell, a),
-                       np.tile(v, (ncell, 1)), np.asarray(sensors, dtype=np.int64), beta[0], beta[1])
+                       np.tile(v, (ncell, 1)), np.asarray(sensors, dtype=np.int64), beta[0], beta[1], reg)
 
 
 def _sxyz(xyz):
@@ -267,3 +268,53 @@ def test_micro_kkt_solution_is_consistent_with_marching():
     Wm = p0.beta1 * sp.kron(p0.Lt, p0.B) + p0.beta2 * sp.kron(p0.Mt, p0.K)
     grad = Wm @ X[:, :, 2].ravel() - sp.kron(p0.Mt, p0.B) @ Gm.ravel()
     assert np.abs(grad).max() < 1e-10 * np.abs(Wm @ X[:, :, 2].ravel()).max()
+
+
+@pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
+def test_regulariser_rows_on_constant_source_closed_form(reg):
+    """F_h applied to (C, G, f) = (0, 0, 1): the time stiffness and the spatial stiffness
+    annihilate constants, so the f rows are 0 for H1-H1 (Eq. 3) and beta2 (int psi_n dt)
+    (int phi_j dx) for H1-L2 (Example 2); the C rows are -tau (int phi_j dx) off the
+    Dirichlet nodes for both.  The integrals of the hat functions are written out from the
+    grid (h/2 at an end node, h inside), not taken from the oracle's matrices."""
+    c, M = 3, 4
+    p = _cube_problem(c, M, faces=W.FACE_X0, beta=(2e-3, 5e-2), reg=reg)
+    h, tau = 1.0 / c, p.tau
+    w1 = np.full(c + 1, h)
+    w1[[0, -1]] = h / 2
+    phi = np.einsum("k,j,i->kji", w1, w1, w1).ravel()      # node order x fastest
+    psi = np.full(M + 1, tau)
+    psi[[0, -1]] = tau / 2
+    U = np.zeros(p.n)
+    U[2::3] = 1.0
+    y = kkt.apply(p, U).reshape(M + 1, p.N, 3)
+    want_f = np.zeros((M + 1, p.N)) if reg == "h1h1" else p.beta2 * np.outer(psi, phi)
+    np.testing.assert_allclose(y[:, :, 2], want_f, rtol=1e-13, atol=1e-16)
+    free = ~p.dirichlet
+    np.testing.assert_allclose(y[1:, free, 0], -tau * np.tile(phi[free], (M, 1)), rtol=1e-13, atol=1e-17)
+    np.testing.assert_array_equal(y[:, :, 1], 0.0)
+
+
+@pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
+def test_regulariser_energy_of_a_multilinear_source_is_exact(reg):
+    """f = (1+x)(1+2y)(2-z)(1+t) is its own Q1 x P1 interpolant, and the element mass and
+    stiffness integrals are exact for it, so f . (F_h (0, 0, f))_f equals the regulariser
+    2 N_beta(f) in closed form: beta1 int int f_t^2 + beta2 int int |grad f|^2 (H1-H1) or
+    beta2 int int f^2 (H1-L2), on the unit cube over T = 1."""
+    c, M = 3, 4
+    p = _cube_problem(c, M, beta=(2e-3, 5e-2), reg=reg)
+    xyz = _coords(p)
+    x, y_, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+    t = np.arange(M + 1) * p.tau
+    f = np.outer(1 + t, (1 + x) * (1 + 2 * y_) * (2 - z))
+    U = np.zeros(p.n)
+    U[2::3] = f.ravel()
+    Y = kkt.apply(p, U)[2::3]
+    X2, Y2, Z2, T2 = 7 / 3, 13 / 3, 7 / 3, 7 / 3            # integrals of (1+x)^2, (1+2y)^2, (2-z)^2, (1+t)^2
+    time_term = X2 * Y2 * Z2 * 1.0                           # f_t = (1+x)(1+2y)(2-z)
+    if reg == "h1h1":
+        space_term = (Y2 * Z2 + 4 * X2 * Z2 + X2 * Y2) * T2  # |grad f|^2 over the cube and [0, 1]
+    else:
+        space_term = X2 * Y2 * Z2 * T2
+    want = p.beta1 * time_term + p.beta2 * space_term
+    assert abs(f.ravel() @ Y - want) <= 1e-12 * want
