@@ -93,6 +93,19 @@ kkt_status kkt_create(const kkt_grid* g, int nt, double dt, const double* a_cell
                       const double* v_cell, const int* sensor_node, int nsens,
                       double beta1, double beta2, double theta, kkt_problem** out);
 
+/*
+ * kkt_set_regularization -- choose the source regularisation of the f rows.
+ *   reg 0: H1-H1, N_beta of Eq. 3 (the default after kkt_create): the beta2
+ *          term of W^{nm} is beta2 Mt[n,m] K (the (grad f, grad g) form of Eq. 9);
+ *   reg 1: H1-L2 of Sec. 4 (Example 2), beta2 |grad f|^2 replaced by beta2 f^2:
+ *          the beta2 term is beta2 Mt[n,m] B.
+ * kkt_apply, kkt_residual and gmres_solve read the setting at each call;
+ * ras_setup / coarse_setup (and their refactorisations) build their matrices
+ * from it, so set it before creating the preconditioners of this problem.
+ * Host only, no device work.  Errors: ARG (null problem, reg not 0 or 1).
+ */
+kkt_status kkt_set_regularization(kkt_problem* p, int reg);
+
 /* Sizes of a problem: nodes per axis, N, levels M+1 and unknowns 3*N*(M+1). */
 kkt_status kkt_sizes(const kkt_problem* p, int* nx, int* ny, int* nz, int* levels,
                      long long* unknowns);

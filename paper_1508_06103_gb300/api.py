@@ -60,8 +60,15 @@ class Problem:
 
     @classmethod
     def from_workload(cls, w, cells=None, M=None) -> "Problem":
-        return cls(w.cells, w.lengths, w.M, w.tau, w.a_cell, w.v_cell, w.sensor_nodes(), w.beta1, w.beta2,
-                   w.theta, w.dirichlet_faces)
+        p = cls(w.cells, w.lengths, w.M, w.tau, w.a_cell, w.v_cell, w.sensor_nodes(), w.beta1, w.beta2,
+                w.theta, w.dirichlet_faces)
+        if getattr(w, "reg", "h1h1") != "h1h1":
+            p.set_regularization(w.reg)
+        return p
+
+    def set_regularization(self, reg: str) -> None:
+        """'h1h1' (N_beta, Eq. 3) or 'h1l2' (Sec. 4, Example 2); before building preconditioners."""
+        check(self._lib.kkt_set_regularization(self.h, {"h1h1": 0, "h1l2": 1}[reg]), "kkt_set_regularization")
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_chunks(DevProblem p, co
       Bv = cf.B[ci];
       Sv = cf.S[ci];
       STv = cf.ST[ci];
-      Kv = cf.K[ci];
+      Kv = p.reg ? Bv : cf.K[ci];   // beta2 term: K (H1-H1) or B (H1-L2)
     }
     constexpr int kCentre = 13;
     // C row

@@ -60,6 +60,7 @@ struct DevProblem {
   int nx, ny, nz, N, M, L;
   long long P;                              // points N * (M+1)
   double tau, theta, beta1, beta2;
+  int reg;                                  // beta2 term: 0 stiffness K (H1-H1), 1 mass B (H1-L2)
   double hx, hy, hz;                        // mesh widths (B and K are tensor products of 1D factors)
   const double *S, *ST, *B, *K;             // [27][N] row coefficients (FP64)
   const float *S32, *ST32, *B32, *K32;      // FP32 copies
@@ -88,6 +89,7 @@ struct kkt_problem {
   int nx, ny, nz, N, M, L;
   long long P, n;                           // points, unknowns
   double hx, hy, hz, tau, T, theta, beta1, beta2;
+  int reg = 0;                              // kkt_set_regularization
   // host copies used by the coarse level
   std::vector<double> a_cell, v_cell;
   std::vector<int> sensor_node;

@@ -43,7 +43,8 @@ __device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
 //   u3 = G^n - G^{n+1}                                              (G row, via B)
 //   u4 = tau (theta G^n + (1-theta) G^{n+1})                        (G row, via S^T)
 //   u5 = -(Mt G)_n + beta1 (Lt f)_n                                 (f row, via B)
-//   u6 = beta2 (Mt f)_n                                             (f row, via K)
+//   u6 = beta2 (Mt f)_n                                             (f row, via K;
+//        via B, added to u5, under the H1-L2 regularisation)
 // are formed once per halo node.  B = Mx (x) My (x) Mz and K = Kx My Mz +
 // Mx Ky Mz + Mx My Kz are tensor products of the 1D linear-element mass and
 // stiffness matrices on the uniform grid, so B u1, B u3, B u5 and K u6 are
@@ -149,7 +150,9 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <typename T>
+// kL2: the H1-L2 regularisation (its beta2 term goes through B), a template
+// argument so the H1-H1 kernel carries no test for it.
+template <typename T, bool kL2>
 __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T* __restrict__ x,
                                                            T* __restrict__ y, const double* __restrict__ b,
                                                            int tiles_x, int tiles_y, Axis1D<T> ax, Axis1D<T> ay,
@@ -222,8 +225,11 @@ __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T
       U[NH + h] = wt0 * C0 + wt1 * Cm;
       U[2 * NH + h] = G0 - Gp;
       U[3 * NH + h] = wt0 * G0 + wt1 * Gp;
-      U[4 * NH + h] = (lm * Fm + l0 * F0 + lp * Fp) - (mtm * Gm + mt0 * G0 + mtp * Gp);
-      U[5 * NH + h] = km * Fm + k0 * F0 + kp * Fp;
+      const T u5 = (lm * Fm + l0 * F0 + lp * Fp) - (mtm * Gm + mt0 * G0 + mtp * Gp);
+      const T u6 = km * Fm + k0 * F0 + kp * Fp;
+      // H1-L2: the beta2 term goes through B with u5 (B u5 + B u6), and K sees 0
+      U[4 * NH + h] = kL2 ? u5 + u6 : u5;
+      U[5 * NH + h] = kL2 ? (T)0 : u6;
     }
     __syncthreads();
     if (n + 3 <= n1) prefetch(n + 3);    // into the slot of level n - 1, no longer read
@@ -310,8 +316,13 @@ void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaSt
   az.init(p.nz, p.hz);
   LevelW<T> w;
   w.init(p.tau, p.theta, p.beta1, p.beta2);
-  cudaFuncSetAttribute(matvec_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T>());
-  matvec_tiled<T><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+  if (p.reg != 0) {
+    cudaFuncSetAttribute(matvec_tiled<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T>());
+    matvec_tiled<T, true><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+  } else {
+    cudaFuncSetAttribute(matvec_tiled<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T>());
+    matvec_tiled<T, false><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+  }
 }
 
 __global__ void d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {

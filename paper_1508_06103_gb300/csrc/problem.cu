@@ -90,7 +90,7 @@ extern "C" const char* kkt_version(void) { return "stkkt 0.1 (sm_103a)"; }
 DevProblem kkt_problem::dev() const {
   DevProblem d;
   d.nx = nx; d.ny = ny; d.nz = nz; d.N = N; d.M = M; d.L = L; d.P = P;
-  d.tau = tau; d.theta = theta; d.beta1 = beta1; d.beta2 = beta2;
+  d.tau = tau; d.theta = theta; d.beta1 = beta1; d.beta2 = beta2; d.reg = reg;
   d.hx = hx; d.hy = hy; d.hz = hz;
   const size_t c = (size_t)kStencil * N;
   d.S = coef64; d.ST = coef64 + c; d.B = coef64 + 2 * c; d.K = coef64 + 3 * c;
@@ -306,6 +306,15 @@ extern "C" kkt_status kkt_create(const kkt_grid* g, int nt, double dt, const dou
                                  const int* sensor_node, int nsens, double beta1, double beta2, double theta,
                                  kkt_problem** out) {
   return create_problem(g, nt, dt, a_cell, v_cell, sensor_node, nsens, beta1, beta2, theta, out);
+}
+
+extern "C" kkt_status kkt_set_regularization(kkt_problem* p, int reg) {
+  if (!p || (reg != 0 && reg != 1)) {
+    set_error("kkt_set_regularization: null problem, or reg not 0 (H1-H1) or 1 (H1-L2)");
+    return KKT_ERR_ARG;
+  }
+  p->reg = reg;
+  return KKT_OK;
 }
 
 extern "C" kkt_status kkt_sizes(const kkt_problem* p, int* nx, int* ny, int* nz, int* levels, long long* unknowns) {

@@ -90,7 +90,7 @@ __device__ __forceinline__ T slot_value(const DevProblem& p, const BoxDesc& bx, 
   }
   const T mt1 = tau / (T)6, lt1 = -(T)1 / tau;
   const T mt = dt == 0 ? pr.mt0 : mt1, lt = dt == 0 ? pr.lt0 : lt1;
-  return cc == 1 ? -mt * cf.B[ci] : b1 * lt * cf.B[ci] + b2 * mt * cf.K[ci];
+  return cc == 1 ? -mt * cf.B[ci] : b1 * lt * cf.B[ci] + b2 * mt * (p.reg ? cf.B[ci] : cf.K[ci]);
 }
 
 }  // namespace

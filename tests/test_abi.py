@@ -69,4 +69,6 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
     assert lib.kkt_create(ctypes.byref(g), 4, 0.25, a, v, s, 1, 1e-3, 1e-1, 0.5, ctypes.byref(h)) == -1
     assert b"sensor" in lib.kkt_last_error()
     assert lib.kkt_apply(None, None, None, 64, None) == -1
+    assert lib.kkt_set_regularization(None, 1) == -1
+    assert b"kkt_set_regularization" in lib.kkt_last_error()
     assert lib.gmres_solve(None, None, None, None, None, 30, 1e-8, 10, 0, None, None, None) == -1

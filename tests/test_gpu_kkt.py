@@ -37,14 +37,15 @@ CASES = [
 ]
 
 
-def _case(c):
+def _case(c, reg="h1h1"):
     return W.random_small(c["seed"], cells=c["cells"], M=c["M"], theta=c["theta"], dirichlet_faces=c["faces"],
-                          nsens=7)
+                          nsens=7, reg=reg)
 
 
+@pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c["cells"])) + f"x{c['M']}")
-def test_matvec_fp64_matches_oracle_csr(api, case):
-    w = _case(case)
+def test_matvec_fp64_matches_oracle_csr(api, case, reg):
+    w = _case(case, reg)
     F = okkt.assemble(okkt.Problem.from_workload(w))
     prob = api.Problem.from_workload(w)
     assert prob.n == F.shape[0]

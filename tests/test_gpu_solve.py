@@ -22,6 +22,8 @@ Tolerances:
   oracle's FP64 ILU(0) apply <= 8 u_bf16 (u = 2^-8).
 """
 
+import dataclasses
+
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -56,9 +58,10 @@ RAS_CASES = [
 ]
 
 
+@pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
 @pytest.mark.parametrize("case", RAS_CASES, ids=["2x2x1x2", "3x2x2x3-ov2", "single"])
-def test_ras_apply_fp64_matches_oracle(api, case):
-    w = W.random_small(nsens=6, **case["w"])
+def test_ras_apply_fp64_matches_oracle(api, case, reg):
+    w = W.random_small(nsens=6, reg=reg, **case["w"])
     p = okkt.Problem.from_workload(w)
     F = okkt.assemble(p)
     ref = osch.RAS(p, F, case["nsub"], case["ov"], "ilu0")
@@ -71,13 +74,14 @@ def test_ras_apply_fp64_matches_oracle(api, case):
         assert np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
 
 
+@pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
 @pytest.mark.parametrize("case", RAS_CASES, ids=["2x2x1x2", "3x2x2x3-ov2", "single"])
-def test_ras_apply_exact_lu_matches_oracle(api, case):
+def test_ras_apply_exact_lu_matches_oracle(api, case, reg):
     # Both sides solve the same box matrices exactly (GPU: band LU with partial
     # pivoting; oracle: sparse LU), each backward stable, so each box's
     # solution differs by at most ~cond_1(M_ij) u times a modest growth factor:
     # bar 100 cond_1 u max|z| with the largest cond_1 of the boxes.
-    w = W.random_small(nsens=6, **case["w"])
+    w = W.random_small(nsens=6, reg=reg, **case["w"])
     p = okkt.Problem.from_workload(w)
     F = okkt.assemble(p)
     ref = osch.RAS(p, F, case["nsub"], case["ov"], "lu")
@@ -147,8 +151,10 @@ def _two_level_case():
     return W.mid(cells=(4, 4, 4), M=8, nsub=(2, 2, 2, 2), overlap=1, coarse_cells=(2, 2, 2), coarse_M=4)
 
 
-def test_two_level_apply_fp64_matches_oracle(api):
-    w = _two_level_case()
+@pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
+def test_two_level_apply_fp64_matches_oracle(api, reg):
+    # under H1-L2 this also checks that the coarse level takes the fine level's regularisation
+    w = dataclasses.replace(_two_level_case(), reg=reg)
     p = okkt.Problem.from_workload(w)
     F = okkt.assemble(p)
     ref = osch.TwoLevel(p, F, w.nsub, w.overlap, w.coarse_cells, w.coarse_M, 1, 0.1, 4, "ilu0")
