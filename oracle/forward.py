@@ -13,6 +13,10 @@ adjoint_march : G^M = 0, then for n = M-1..0 solve
                 with G = 0 on the Dirichlet nodes.
 observations  : C at the sensor nodes with multiplicative noise
                 C^eps = C + eps r C (Sec. 4), r passed in.
+observations_refined : the same from a forward solve on a mesh `refine`
+                times finer in space and time (Sec. 4 generates the data "on a
+                very fine mesh with a small time step"), sampled at the coarse
+                levels 0, refine, 2 refine, ...
 
 The linear solves use scipy's sparse LU (a library routine as one step).
 
@@ -84,4 +88,19 @@ def adjoint_march(p: Problem, C: np.ndarray, c_obs: np.ndarray,
 def observations(p: Problem, C: np.ndarray, r: np.ndarray, eps: float) -> np.ndarray:
     """C^eps at the sensors, shape (M+1, s): C + eps r C (Sec. 4)."""
     Cs = C[:, p.sensor_node]
+    return Cs + eps * r * Cs
+
+
+def observations_refined(p_fine: Problem, f_fine: np.ndarray, refine: int, r: np.ndarray,
+                         eps: float) -> np.ndarray:
+    """C^eps at the sensors of p_fine on every refine-th level, shape (M_fine/refine + 1, s).
+
+    p_fine is the problem on the refined mesh (its sensors at nodes of the coarse
+    mesh), f_fine the true source at its nodes and levels, r the noise draws of
+    the coarse samples.
+    """
+    if p_fine.M % refine:
+        raise ValueError("the fine level count must be a multiple of the refinement")
+    C = forward_march(p_fine, f_fine)
+    Cs = C[::refine, p_fine.sensor_node]
     return Cs + eps * r * Cs

@@ -277,6 +277,28 @@ def random_small(seed: int, cells=(5, 4, 3), M: int = 5, theta: float = 0.5,
     )
 
 
+def refined(w: Workload, r: int) -> Workload:
+    """The same problem on a mesh r times finer in space and time, for data generation.
+
+    Sec. 4 generates the observations by a forward solve "on a finer mesh with a
+    smaller time step".  Each fine cell keeps the diffusivity and velocity of the
+    cell it lies in (so every refinement discretises the same coefficients), the
+    sensors sit at the coordinates of the nodes the coarse mesh snaps them to
+    (nodes of every refinement), and the sources, noise draws and the rest are
+    unchanged; the coarse levels are the fine levels 0, r, 2r, ...
+    """
+    if r < 1:
+        raise ValueError("refinement factor must be >= 1")
+    cx, cy, cz = w.cells
+    fx, fy, fz = cx * r, cy * r, cz * r
+    kz, ky, kx = np.meshgrid(np.arange(fz) // r, np.arange(fy) // r, np.arange(fx) // r, indexing="ij")
+    parent = (kx + cx * (ky + cy * kz)).ravel()
+    sens = w.node_coords()[w.sensor_nodes()]
+    return dataclasses.replace(w, name=f"{w.name}_refined{r}", cells=(fx, fy, fz), M=w.M * r,
+                               a_cell=np.asarray(w.a_cell)[parent], v_cell=np.asarray(w.v_cell)[parent],
+                               sensor_xyz=sens)
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded standard normal vector."""
     return np.random.Generator(np.random.PCG64(seed)).standard_normal(n)

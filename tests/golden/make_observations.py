@@ -1,14 +1,16 @@
 """Write the noisy sensor observations of the 32^3 x 64 workload (oracle only).
 
 The data follow Sec. 4 of the paper: the forward problem is solved with the
-true source (here on the same mesh and scheme; the paper uses a finer mesh)
-and the sensor values get multiplicative Gaussian noise C + eps r C.  The
+true source (by default on the same mesh and scheme; with --refine R on a mesh
+R times finer in space and time, as the paper does) and the sensor values get
+multiplicative Gaussian noise C + eps r C.  The
 forward solve is the oracle's time march; the seeded inputs (grid,
 coefficients, sensors, source, noise draws r) come from the workload module.
 The benchmark reads the resulting text file so that it never runs the oracle
 outside its CPU-baseline leg.
 
-    python tests/golden/make_observations.py
+    python tests/golden/make_observations.py              # observations_mid_32x32x32x64.txt
+    python tests/golden/make_observations.py --refine 2   # ..._refined2.txt (not used by default)
 """
 
 import os
@@ -23,15 +25,27 @@ from oracle import forward, kkt  # noqa: E402
 from paper_1508_06103_gb300 import workloads as W  # noqa: E402
 
 
-def write(w, path):
-    p = kkt.Problem.from_workload(w)
-    C = forward.forward_march(p, w.true_source())
-    obs = forward.observations(p, C, w.noise(), w.noise_eps)
-    header = (f"noisy observations C + eps r C at {len(p.sensor_node)} sensors x {p.L} levels, "
-              f"workload {w.name}, eps {w.noise_eps}, noise seed {w.noise_seed}; row = time level")
+def write(w, path, refine=1):
+    if refine == 1:
+        p = kkt.Problem.from_workload(w)
+        C = forward.forward_march(p, w.true_source())
+        obs = forward.observations(p, C, w.noise(), w.noise_eps)
+    else:
+        wf = W.refined(w, refine)
+        obs = forward.observations_refined(kkt.Problem.from_workload(wf), wf.true_source(), refine, w.noise(),
+                                           w.noise_eps)
+    fine = "" if refine == 1 else f", forward solve on a mesh refined {refine}x"
+    header = (f"noisy observations C + eps r C at {obs.shape[1]} sensors x {obs.shape[0]} levels, "
+              f"workload {w.name}, eps {w.noise_eps}, noise seed {w.noise_seed}{fine}; row = time level")
     np.savetxt(path, obs, fmt="%.17g", header=header)
 
 
 if __name__ == "__main__":
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--refine", type=int, default=1)
+    a = ap.parse_args()
     w = W.mid()
-    write(w, os.path.join(HERE, f"observations_{w.name}.txt"))
+    suffix = "" if a.refine == 1 else f"_refined{a.refine}"
+    write(w, os.path.join(HERE, f"observations_{w.name}{suffix}.txt"), a.refine)
