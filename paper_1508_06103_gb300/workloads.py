@@ -35,12 +35,16 @@ ALL_FACES = 63
 
 @dataclasses.dataclass
 class Source:
-    """One Gaussian source amp * exp(-|x - c(t)|^2 / (2 sigma^2)) * w(t)."""
+    """One source times a switch w(t), centred at c(t): a Gaussian
+    amp * exp(-|x - c(t)|^2 / (2 sigma^2)), or with shape "box" the constant amp
+    on the cube max_k |x_k - c_k(t)| < half_width."""
 
     center: Callable[[float], Tuple[float, float, float]]
     sigma: float = 0.1
     amp: float = 1.0
     switch: Callable[[float], float] = lambda t: 1.0
+    shape: str = "gaussian"
+    half_width: float = 0.4
 
 
 @dataclasses.dataclass
@@ -123,8 +127,12 @@ class Workload:
             t = n * self.tau
             for s in self.sources:
                 c = np.asarray(s.center(t))
-                r2 = ((xyz - c) ** 2).sum(axis=1)
-                out[n] += s.amp * s.switch(t) * np.exp(-r2 / (2.0 * s.sigma ** 2))
+                if s.shape == "box":
+                    inside = (np.abs(xyz - c) < s.half_width).all(axis=1)
+                    out[n] += s.amp * s.switch(t) * inside
+                else:
+                    r2 = ((xyz - c) ** 2).sum(axis=1)
+                    out[n] += s.amp * s.switch(t) * np.exp(-r2 / (2.0 * s.sigma ** 2))
         return out
 
 
@@ -258,6 +266,90 @@ def large() -> Workload:
         nsub=(8, 8, 8, 8), overlap=2, local="ilu0", coarse_cells=(16, 16, 16), coarse_M=32,
         coarse_overlap=1, restart=40, rtol=1e-8,
     )
+
+
+# ---------------------------------------------------------------------------
+# the paper's Examples 1-3 (Sec. 4.1) as synthetic workloads
+# ---------------------------------------------------------------------------
+# Domain (-2, 2)^3 (here [0, 4]^3, paper coordinates shifted by +2), T = 1,
+# C(., 0) = 0, a = 1, v = (1, 1, 1); Dirichlet on |x| = 2 and |y| = 2, Neumann
+# on |z| = 2; Crank-Nicolson.  Sensors: an m^3 lattice inside the domain.  The
+# paper runs these with np = 256 subdomains (4^4 here), overlap 1, ILU(0),
+# one level.  L = S = H = 2 are the half-widths used in the source traces.
+_HALF = 2.0
+
+
+def _paper_example(name, cells, M, sources, sensors, beta1, beta2, noise_eps=0.01, reg="h1h1"):
+    L = (2 * _HALF,) * 3
+    ncell = cells ** 3
+    return Workload(
+        name=name, cells=(cells,) * 3, lengths=L, T=1.0, M=M, theta=0.5,
+        dirichlet_faces=FACE_X0 | FACE_X1 | FACE_Y0 | FACE_Y1,
+        a_cell=np.full(ncell, 1.0), v_cell=np.tile([1.0, 1.0, 1.0], (ncell, 1)),
+        sensor_xyz=sensor_lattice(sensors, L), beta1=beta1, beta2=beta2, sources=sources,
+        noise_eps=noise_eps, noise_seed=11, nsub=(4, 4, 4, 4), overlap=1, local="ilu0",
+        restart=30, rtol=1e-8, reg=reg,
+    )
+
+
+def _shifted(f):
+    """A trace in the paper's coordinates on (-2, 2)^3, moved to [0, 4]^3."""
+    def c(t: float):
+        return tuple(v + _HALF for v in f(t))
+    return c
+
+
+def example1(cells: int = 40, M: int = 39, noise_eps: float = 0.01) -> Workload:
+    """Two moving Gaussians exp(-|x - x_i(t)|^2 / a^2), a = 2 (so sigma = a / sqrt 2);
+    40^3 mesh, tau = 1/39, 14^3 sensors, beta1 = 3.6e-5, beta2 = 3.6e-3."""
+    L = S = H = _HALF
+    tr1 = _shifted(lambda t: (L * math.sin(2 * math.pi * t), S * math.cos(2 * math.pi * t),
+                              H * math.cos(4 * math.pi * t)))
+    tr2 = _shifted(lambda t: (L - 2 * L * abs(math.cos(4 * t)), -S + 2 * S * abs(math.cos(4 * t)),
+                              -H + 2 * H * t * t))
+    sig = 2.0 / math.sqrt(2.0)
+    return _paper_example(f"example1_{cells}x{M}", cells, M, [Source(tr1, sig), Source(tr2, sig)], 14,
+                          3.6e-5, 3.6e-3, noise_eps)
+
+
+def example2(reg: str = "h1h1", cells: int = 40, M: int = 39) -> Workload:
+    """Four constant cube sources of half-width 0.4 moving along the diagonals to the far
+    corners, amplitudes 2, 1, 1, 2; mesh, sensors as Example 1; beta1 = 1e-5 and beta2 = 1e-3
+    (H1-H1) or 1e-8 (H1-L2)."""
+    L = S = H = _HALF
+    traces = [
+        lambda t: (-L + 2 * L * t, -S + 2 * S * t, H - 2 * H * t),
+        lambda t: (L - 2 * L * t, S - 2 * S * t, -H + 2 * H * t),
+        lambda t: (L - 2 * L * t, -S + 2 * S * t, -H + 2 * H * t),
+        lambda t: (-L + 2 * L * t, S - 2 * S * t, H - 2 * H * t),
+    ]
+    amps = (2.0, 1.0, 1.0, 2.0)
+    srcs = [Source(_shifted(tr), amp=a, shape="box", half_width=0.4) for tr, a in zip(traces, amps)]
+    beta2 = 1e-3 if reg == "h1h1" else 1e-8
+    return _paper_example(f"example2_{reg}_{cells}x{M}", cells, M, srcs, 14, 1e-5, beta2, reg=reg)
+
+
+def example3(sensors: int = 21, cells: int = 64, M: int = 47) -> Workload:
+    """Eight Gaussians a_i exp(-|x - x_i(t)|^2) starting at the corners (the printed exponent's
+    parentheses are garbled; read as -|x - x_i|^2, so sigma = 1/sqrt 2), a = 4 (i <= 4), 6;
+    64^3 mesh, tau = 1/47, 21^3 or 9^3 sensors, beta1 = 3.6e-5, beta2 = 3.6e-1."""
+    L = S = H = _HALF
+    c2, s2 = (lambda t, k=1.0: math.cos(k * math.pi * t) ** 2), (lambda t: math.sin(math.pi * t) ** 2)
+    ch, sh = (lambda t: math.cos(math.pi / 2 * t)), (lambda t: math.sin(math.pi / 2 * t))
+    traces = [
+        lambda t: (-L + 2 * L * (1 - t), -S + 2 * S * (1 - t), -H + 2 * H * (1 - t)),
+        lambda t: (-L + 2 * L * t, -S + 2 * S * t, -H + 2 * H * t),
+        lambda t: (-L + 2 * L * c2(t) * (1 - t), -S + 2 * S * s2(t) * t, -H + 2 * H * c2(t) * (1 - t)),
+        lambda t: (-L + 2 * L * c2(t) * (1 - t), -S + 2 * S * c2(t) * (1 - t), -H + 2 * H * s2(t) * t),
+        lambda t: (-L + 2 * L * c2(t, 2.0) * ch(t), -S + 2 * S * s2(t) * sh(t), -H + 2 * H * s2(t) * sh(t)),
+        lambda t: (-L + 2 * L * s2(t) * sh(t), -S + 2 * S * c2(t, 2.0) * ch(t), -H + 2 * H * s2(t) * sh(t)),
+        lambda t: (-L + 2 * L * s2(t) * sh(t), -S + 2 * S * s2(t) * sh(t), -H + 2 * H * c2(t, 2.0) * ch(t)),
+        lambda t: (-L + 2 * L * s2(t) * sh(t), -S + 2 * S * c2(t, 2.0) * ch(t), -H + 2 * H * c2(t, 2.0) * ch(t)),
+    ]
+    amps = (4.0,) * 4 + (6.0,) * 4
+    sig = 1.0 / math.sqrt(2.0)
+    srcs = [Source(_shifted(tr), sig, a) for tr, a in zip(traces, amps)]
+    return _paper_example(f"example3_s{sensors}_{cells}x{M}", cells, M, srcs, sensors, 3.6e-5, 3.6e-1)
 
 
 def random_small(seed: int, cells=(5, 4, 3), M: int = 5, theta: float = 0.5,
