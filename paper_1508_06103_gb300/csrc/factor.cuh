@@ -106,11 +106,11 @@ __device__ __forceinline__ void check_pivot(double d, int* status) {
 
 template <typename T>
 __global__ void __launch_bounds__(factor_threads<T>, 2) ilu0_factor(const BoxDesc* __restrict__ boxes,
-                                                                 const int* __restrict__ iperm,
-                                                                 const int* __restrict__ perm,
-                                                                 const int* __restrict__ lptr,
-                                                                 const int2* __restrict__ ptab, T* __restrict__ F,
-                                                                 int* __restrict__ status) {
+                                                                    const int* __restrict__ iperm,
+                                                                    const int* __restrict__ perm,
+                                                                    const int* __restrict__ lptr,
+                                                                    const int2* __restrict__ ptab,
+                                                                    T* __restrict__ F, int* __restrict__ status) {
   // per thread and pivot point: {offset of its column in Fb, row stride of its block}
   constexpr int NS = factor_threads<T>;
   __shared__ int2 nbs[kGenNbrs * NS];
