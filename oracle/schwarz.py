@@ -11,7 +11,9 @@ Test infrastructure (see the package header).
   unknowns of every point), which equals the discretisation of Eq. 10 with
   the homogeneous Dirichlet conditions Eqs. 11-12 on the cut faces.
 * Local solvers: ILU(0) on the structural pattern of F_h (the stencil of
-  each block row, textbook IKJ order), or exact sparse LU (scipy, as one step).
+  each block row, textbook IKJ order), ILU(k) (the same elimination on the
+  pattern grown by levels of fill up to k, Table 1), or exact sparse LU
+  (scipy, as one step).
 * One-level restricted additive Schwarz, the cited Cai-Sarkis form
       z = sum_ij (R^0_ij)^T  M_ij^{-1}  R^delta_ij r
   (restricted prolongation); variant="harmonic" gives the literal operand
@@ -153,6 +155,48 @@ class ILU0:
         return self.U[i].get(j, 0.0)
 
 
+def iluk_pattern(Aloc: sp.csr_matrix, pattern: List[np.ndarray], k: int) -> List[np.ndarray]:
+    """Structural pattern of ILU(k) by levels of fill (Sec. 4, Table 1: ILU(k) subdomain solves).
+
+    An entry of the given pattern has level 0.  Eliminating row i in IKJ order, each
+    kept lower entry (i, m) meets each upper entry (m, j) of row m and proposes
+    (i, j) with level lev(i, m) + lev(m, j) + 1; an entry is kept when its smallest
+    proposed level is <= k.  Rows are processed in order, the lower entries of a
+    row in ascending column order (a fill entry left of the diagonal joins the
+    queue), so every lev(i, m) is final when it is used.
+    """
+    import heapq
+
+    n = Aloc.shape[0]
+    ulev: List[dict] = []
+    out = []
+    for i in range(n):
+        lev = {int(c): 0 for c in pattern[i] if c < n}
+        heap = [c for c in lev if c < i]
+        heapq.heapify(heap)
+        done = set()
+        while heap:
+            m = heapq.heappop(heap)
+            if m in done:
+                continue
+            done.add(m)
+            lm = lev[m]
+            for j, lmj in ulev[m].items():
+                nl = lm + lmj + 1
+                if nl > k:
+                    continue
+                if j in lev:
+                    if nl < lev[j]:
+                        lev[j] = nl
+                else:
+                    lev[j] = nl
+                    if j < i:
+                        heapq.heappush(heap, j)
+        ulev.append({j: l for j, l in lev.items() if j > i})
+        out.append(np.array(sorted(lev), dtype=np.int64))
+    return out
+
+
 class ExactLU:
     """Exact local solve by sparse LU (scipy's SuperLU as one step)."""
 
@@ -195,6 +239,8 @@ class RAS:
             Aloc = F[idx][:, idx].tocsr()
             if local == "ilu0":
                 solver = ILU0(Aloc, local_pattern(p, idx))
+            elif local.startswith("ilu"):   # "ilu1", "ilu2", ...: ILU(k) on the level-k pattern
+                solver = ILU0(Aloc, iluk_pattern(Aloc, local_pattern(p, idx), int(local[3:])))
             elif local == "lu":
                 solver = ExactLU(Aloc)
             else:

@@ -200,3 +200,64 @@ def test_partial_ilu0_is_the_leading_block_of_the_full_one():
     for i in range(40):
         assert part.L[i] == full.L[i] and part.diag[i] == full.diag[i]
         assert part.U[i] == {j: v for j, v in full.U[i].items() if j < 40}
+
+
+def _laplace5(n):
+    T = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(n, n))
+    A = (sp.kron(sp.eye(n), T) + sp.kron(T, sp.eye(n))).tocsr()
+    A.eliminate_zeros()
+    return A, [A.indices[A.indptr[i]:A.indptr[i + 1]] for i in range(n * n)]
+
+
+def test_iluk_levels_of_fill_on_the_five_point_laplacian():
+    """Textbook levels of fill (Saad, Iterative Methods, Sec. 10.3): on an n x n grid with the
+    5-point stencil, ILU(1) adds the diagonals at offsets +-(n - 1) and ILU(2) also +-(n - 2);
+    each new diagonal has (n - 1)^2 entries."""
+    n = 6
+    A, pat = _laplace5(n)
+    offsets = lambda P: sorted({int(j) - i for i, row in enumerate(P) for j in row})
+    p0, p1, p2 = (schwarz.iluk_pattern(A, pat, k) for k in (0, 1, 2))
+    assert offsets(p0) == [-n, -1, 0, 1, n]
+    assert offsets(p1) == [-n, -(n - 1), -1, 0, 1, n - 1, n]
+    assert offsets(p2) == [-n, -(n - 1), -(n - 2), -1, 0, 1, n - 2, n - 1, n]
+    nnz = lambda P: sum(len(r) for r in P)
+    assert nnz(p1) - nnz(p0) == 2 * (n - 1) ** 2
+    assert all(set(a.tolist()) <= set(b.tolist()) for a, b in zip(p1, p2))
+
+
+def test_iluk_on_a_kkt_box_has_the_ilu_property_and_reaches_exact_lu():
+    p, F = _small()
+    b = schwarz.boxes(p, (2, 1, 1, 2), 1)[1]
+    idx, _ = schwarz.box_unknowns(p, b)
+    A = F[idx][:, idx].tocsr()
+    pat = schwarz.local_pattern(p, idx)
+    n = len(idx)
+    assert [r.tolist() for r in schwarz.iluk_pattern(A, pat, 0)] == [sorted(r.tolist()) for r in pat]
+    p1 = schwarz.iluk_pattern(A, pat, 1)
+    ilu = schwarz.ILU0(A, p1)
+    Lm, Um = np.eye(n), np.zeros((n, n))
+    for i in range(n):
+        for k, v in ilu.L[i].items():
+            Lm[i, k] = v
+        Um[i, i] = ilu.diag[i]
+        for j, v in ilu.U[i].items():
+            Um[i, j] = v
+    mask = np.zeros((n, n), dtype=bool)
+    for i, cols in enumerate(p1):
+        mask[i, cols] = True
+    Ad = A.toarray()
+    assert np.abs((Lm @ Um - Ad)[mask]).max() < 1e-13 * np.abs(Ad).max()
+    assert sum(len(r) for r in p1) > sum(len(r) for r in pat)
+    # with a level above any path length the pattern is the full fill: exact LU
+    full = schwarz.ILU0(A, schwarz.iluk_pattern(A, pat, n))
+    r = W.random_vector(n, 5)
+    np.testing.assert_allclose(full.solve(r), np.linalg.solve(Ad, r), rtol=1e-9, atol=1e-12)
+
+
+def test_higher_fill_level_needs_no_more_iterations():
+    """Table 1's trend: more fill, fewer (or equal) preconditioned iterations."""
+    p, F = _small(cells=(4, 3, 3), M=5)
+    bvec = W.random_vector(p.n, 2)
+    its = [krylov.gmres(lambda u: F @ u, bvec, schwarz.RAS(p, F, (2, 2, 2, 2), 1, loc).apply, restart=60,
+                        rtol=1e-8).iterations for loc in ("ilu0", "ilu1", "lu")]
+    assert its[0] >= its[1] >= its[2], its
