@@ -22,7 +22,8 @@ The linear solves use scipy's sparse LU (a library routine as one step).
 
 Pins: tests/test_oracle_kkt.py (manufactured-solution convergence orders in
 h and tau; the marched (C, f) pair zeroes the C rows of F_h; the marched
-adjoint zeroes the G rows).
+adjoint zeroes the G rows) and tests/test_oracle_data.py (refining by 1 gives the
+same-mesh data; refined data converge at second order).
 """
 
 from __future__ import annotations

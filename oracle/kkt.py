@@ -35,7 +35,8 @@ Neumann data q is zero in all workloads, so its boundary term vanishes.
 
 Pins: tests/test_oracle_kkt.py (two independent constructions agree, block
 transposition B1 = A1^T, forward-march consistency of the state rows,
-convergence orders, exact solves).
+convergence orders, exact solves; both regularisers on a constant source against
+the hat-function integrals and on a multilinear source against its exact energy).
 """
 
 from __future__ import annotations

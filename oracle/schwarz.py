@@ -30,7 +30,9 @@ Test infrastructure (see the package header).
 Pins: tests/test_oracle_schwarz.py (ILU(0) defining property (LU)_ij = a_ij
 on the pattern, ILU(0) = LU without fill, one box with exact LU = exact
 inverse, interpolation reproduces multilinear functions, <Pu, w> = <u, P^T w>,
-coarse mesh equal to fine mesh with an exact coarse solve is exact).
+coarse mesh equal to fine mesh with an exact coarse solve is exact; ILU(k):
+the textbook fill diagonals of the 5-point Laplacian for k = 1, 2, the ILU
+property on the level-1 pattern of a KKT box, exact LU at a high level).
 """
 
 from __future__ import annotations
