@@ -18,7 +18,9 @@ observations_refined : the same from a forward solve on a mesh `refine`
                 very fine mesh with a small time step"), sampled at the coarse
                 levels 0, refine, 2 refine, ...
 
-The linear solves use scipy's sparse LU (a library routine as one step).
+The linear solves use scipy's sparse LU (a library routine as one step); on
+meshes whose LU fill is too large, Jacobi-preconditioned BiCGSTAB to a relative
+residual of 1e-13 per step instead.
 
 Pins: tests/test_oracle_kkt.py (manufactured-solution convergence orders in
 h and tau; the marched (C, f) pair zeroes the C rows of F_h; the marched
@@ -40,15 +42,38 @@ def _dirichlet_rows(Mat: sp.csr_matrix, D: np.ndarray) -> sp.csr_matrix:
     return (keep @ Mat + sp.diags(D.astype(np.float64))).tocsc()
 
 
+def _step_solver(A: sp.csc_matrix, solver: str, rtol: float):
+    """x = A^{-1} r: sparse LU, or (for meshes whose LU fill is too large) BiCGSTAB with a
+    Jacobi preconditioner to relative residual rtol, started from the previous step."""
+    if solver == "lu":
+        lu = spla.splu(A)
+        return lambda r, x0: lu.solve(r)
+    if solver != "bicgstab":
+        raise ValueError(solver)
+    A = A.tocsr()
+    dinv = 1.0 / A.diagonal()
+    M = spla.LinearOperator(A.shape, matvec=lambda v: dinv * v)
+
+    def solve(r, x0):
+        if not np.any(r):
+            return np.zeros_like(r)
+        x, info = spla.bicgstab(A, r, x0=x0, rtol=rtol, atol=0.0, M=M, maxiter=5000)
+        if info != 0:
+            raise RuntimeError(f"bicgstab did not reach rtol {rtol} (info {info})")
+        return x
+    return solve
+
+
 def forward_march(p: Problem, f: np.ndarray, c0: np.ndarray | None = None,
-                  rhs_extra: np.ndarray | None = None) -> np.ndarray:
+                  rhs_extra: np.ndarray | None = None, solver: str = "lu", rtol: float = 1e-13) -> np.ndarray:
     """State C^0..C^M (shape (M+1, N)) for nodal source values f (shape (M+1, N)).
 
     rhs_extra[n] (n >= 1), if given, is added to the right-hand side of step n
-    (used by the manufactured-solution tests).
+    (used by the manufactured-solution tests).  solver "lu" (default) or
+    "bicgstab" (to relative residual rtol per step).
     """
     th, tau, D = p.theta, p.tau, p.dirichlet
-    lhs = spla.splu(_dirichlet_rows(p.B + th * tau * p.S, D))
+    solve = _step_solver(_dirichlet_rows(p.B + th * tau * p.S, D), solver, rtol)
     R = (p.B - (1.0 - th) * tau * p.S).tocsr()
     C = np.zeros((p.L, p.N))
     if c0 is not None:
@@ -59,7 +84,7 @@ def forward_march(p: Problem, f: np.ndarray, c0: np.ndarray | None = None,
         if rhs_extra is not None:
             r = r + rhs_extra[n]
         r[D] = 0.0
-        C[n] = lhs.solve(r)
+        C[n] = solve(r, C[n - 1])
     return C
 
 
@@ -93,7 +118,7 @@ def observations(p: Problem, C: np.ndarray, r: np.ndarray, eps: float) -> np.nda
 
 
 def observations_refined(p_fine: Problem, f_fine: np.ndarray, refine: int, r: np.ndarray,
-                         eps: float) -> np.ndarray:
+                         eps: float, solver: str = "lu") -> np.ndarray:
     """C^eps at the sensors of p_fine on every refine-th level, shape (M_fine/refine + 1, s).
 
     p_fine is the problem on the refined mesh (its sensors at nodes of the coarse
@@ -102,6 +127,6 @@ def observations_refined(p_fine: Problem, f_fine: np.ndarray, refine: int, r: np
     """
     if p_fine.M % refine:
         raise ValueError("the fine level count must be a multiple of the refinement")
-    C = forward_march(p_fine, f_fine)
+    C = forward_march(p_fine, f_fine, solver=solver)
     Cs = C[::refine, p_fine.sensor_node]
     return Cs + eps * r * Cs

@@ -32,8 +32,9 @@ def write(w, path, refine=1):
         obs = forward.observations(p, C, w.noise(), w.noise_eps)
     else:
         wf = W.refined(w, refine)
+        # the refined 3D step matrix is too large for sparse LU: BiCGSTAB to 1e-13 per step
         obs = forward.observations_refined(kkt.Problem.from_workload(wf), wf.true_source(), refine, w.noise(),
-                                           w.noise_eps)
+                                           w.noise_eps, solver="bicgstab")
     fine = "" if refine == 1 else f", forward solve on a mesh refined {refine}x"
     header = (f"noisy observations C + eps r C at {obs.shape[1]} sensors x {obs.shape[0]} levels, "
               f"workload {w.name}, eps {w.noise_eps}, noise seed {w.noise_seed}{fine}; row = time level")

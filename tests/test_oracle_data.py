@@ -46,3 +46,13 @@ def test_refined_data_converge_at_second_order():
     e1, e2 = np.linalg.norm(d1 - d4), np.linalg.norm(d2 - d4)
     assert e1 < 0.1 * np.linalg.norm(d4)
     assert e1 / e2 > 3.8, e1 / e2
+
+
+def test_iterative_step_solver_matches_sparse_lu():
+    """The BiCGSTAB step solve (for refined meshes) reproduces the sparse-LU march."""
+    w = W.tiny(theta=0.5)
+    p = kkt.Problem.from_workload(w)
+    f = w.true_source()
+    a = forward.forward_march(p, f)
+    b = forward.forward_march(p, f, solver="bicgstab")
+    assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
