@@ -162,7 +162,7 @@ def oracle_sample(iterations: int, budget_rows: int = 15000):
     t_mv = time.time() - t
     t = time.time()
     for _ in range(4):
-        float(x @ x)
+        float(np.add.reduce(x * x))   # numpy's own loop: one thread (a BLAS dot may use several)
     t_dot = (time.time() - t) / 4
 
     def box_costs(pp, nsub, overlap, rows):
@@ -195,7 +195,7 @@ def oracle_sample(iterations: int, budget_rows: int = 15000):
     est = fac_f + fac_c + iterations * per_iter
     sample = (f"oracle (numpy/scipy, FP64, single-threaded Python loops) on the 32^3x64 workload: one level-wise "
               f"KKT matvec ({t_mv:.2f} s), ILU(0) factor+solve of the leading {rows_f} rows of an interior fine "
-              f"subdomain and {rows_c} rows of a coarse one, numpy dots for CGS2; extrapolated to all subdomain "
+              f"subdomain and {rows_c} rows of a coarse one, single-threaded numpy reductions for CGS2; extrapolated to all subdomain "
               f"rows and {iterations} FGMRES iterations; sample wall {time.time() - t_all:.1f} s")
     return est, sample
 
