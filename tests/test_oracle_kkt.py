@@ -318,3 +318,55 @@ def test_regulariser_energy_of_a_multilinear_source_is_exact(reg):
         space_term = X2 * Y2 * Z2 * T2
     want = p.beta1 * time_term + p.beta2 * space_term
     assert abs(f.ravel() @ Y - want) <= 1e-12 * want
+
+
+def test_known_source_is_recovered_from_noise_free_data_at_small_beta():
+    """Sensors at every node, no noise: as beta -> 0 the KKT solution's source tends to the
+    true one, with an error proportional to beta (the regulariser's bias).  Implicit Euler
+    (theta = 1), levels 1..M: the state sees f^n only through B f^n at n >= 1, so f^0 is
+    fixed by the regulariser alone (with theta = 1/2 the time average of f over each interval
+    is all the state sees, and a time checkerboard is invisible)."""
+    c, M = 4, 6
+    ncell = c ** 3
+    xyz = None
+    errs = []
+    for beta in (1e-7, 1e-9):
+        p = kkt.Problem((c, c, c), (1.0, 1.0, 1.0), 1.0, M, 1.0, 0, np.full(ncell, 0.1),
+                        np.tile([0.3, 0.2, 0.1], (ncell, 1)), np.arange((c + 1) ** 3), beta * 1e-2, beta)
+        xyz = _coords(p)
+        t = np.arange(M + 1) / M
+        ftrue = np.outer(1 + t, np.exp(-((xyz - 0.5) ** 2).sum(axis=1) / 0.1))
+        cobs = forward.forward_march(p, ftrue)[:, p.sensor_node]
+        U = spla.spsolve(kkt.assemble(p).tocsc(), kkt.rhs(p, cobs)).reshape(p.L, p.N, 3)
+        errs.append(np.linalg.norm(U[1:, :, 2] - ftrue[1:]) / np.linalg.norm(ftrue[1:]))
+    assert errs[1] < 1e-2, errs
+    assert errs[0] / errs[1] > 30, errs
+
+
+def test_adjoint_identity_between_state_and_adjoint_rows():
+    """<A u, w> = <u, A^T w> to 1e-12, where A u is taken from the state rows of F_h (C rows,
+    C columns) and A^T w from the adjoint rows (G rows, G columns), which the oracle assembles
+    separately: G^n is the multiplier of the state equation of interval n+1 (slot (G, n)), so
+    the G rows at level n give (A^T w) at level n+1.  u^0 = 0 (C^0 is fixed by the initial
+    condition and has no adjoint equation); no Dirichlet nodes, so no identity rows."""
+    w_ = W.random_small(5, cells=(3, 4, 2), M=5, theta=0.7, dirichlet_faces=0, nsens=5)
+    p = kkt.Problem.from_workload(w_)
+    F = kkt.assemble(p).tocsr()
+    N, M = p.N, p.M
+    ids = lambda n, c: (n * N + np.arange(N)) * 3 + c
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((M + 1, N))
+    u[0] = 0.0
+    wv = rng.standard_normal((M + 1, N))          # wv[n]: multiplier of interval n (n >= 1)
+    wv[0] = 0.0
+    ucol = np.zeros(p.n)
+    ucol[ids(np.arange(M + 1)[:, None], 0).ravel()] = u.ravel()
+    Au = F @ ucol
+    lhs = sum(wv[n] @ Au[ids(n, 0)] for n in range(1, M + 1))
+    gcol = np.zeros(p.n)
+    for n in range(M):
+        gcol[ids(n, 1)] = wv[n + 1]
+    ATw = F @ gcol
+    rhs = sum(u[n + 1] @ ATw[ids(n, 1)] for n in range(M))
+    scale = sum(abs(wv[n]) @ abs(Au[ids(n, 0)]) for n in range(1, M + 1))
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
