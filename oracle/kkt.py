@@ -36,7 +36,9 @@ Neumann data q is zero in all workloads, so its boundary term vanishes.
 Pins: tests/test_oracle_kkt.py (two independent constructions agree, block
 transposition B1 = A1^T, forward-march consistency of the state rows,
 convergence orders, exact solves; both regularisers on a constant source against
-the hat-function integrals and on a multilinear source against its exact energy).
+the hat-function integrals and on a multilinear source against its exact energy;
+the adjoint identity <A u, w> = <u, A^T w> between the state and adjoint rows;
+recovery of a known source from noise-free data as beta -> 0).
 """
 
 from __future__ import annotations
