@@ -43,6 +43,12 @@ sys.path.insert(0, ROOT)
 METRIC = "KKT solve s to 1e-8 rel. residual (mixed vs FP64) at 32^3x64; matvec HBM GB/s"
 UNIT = "s"
 OBS_FILE = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64.txt")
+# the same observations from a forward solve on a 2x finer mesh (the paper's data protocol)
+OBS_FILE_REFINED = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64_refined2.txt")
+
+
+def obs_file(args) -> str:
+    return OBS_FILE_REFINED if getattr(args, "data", "same-mesh") == "refined2" else OBS_FILE
 # Two-level FGMRES(30) iterations of this workload to 1e-8, as the GPU solve
 # measures them; the oracle runs the same algorithm, so its extrapolated solve
 # time uses the same count.
@@ -269,7 +275,7 @@ def gpu_arm(args):
         build.build()
     barrier()
     w = W.mid()
-    cobs_np = np.loadtxt(OBS_FILE, ndmin=2)
+    cobs_np = np.loadtxt(obs_file(args), ndmin=2)
     assert cobs_np.shape == (w.M + 1, len(w.sensor_xyz)), cobs_np.shape
     cobs_host = torch.from_numpy(cobs_np).pin_memory()
     cobs = cobs_host.cuda()
@@ -404,7 +410,9 @@ def gpu_arm(args):
     line = {
         "metric": METRIC, "value": ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w),
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic" + ("" if obs_file(args) == OBS_FILE else " (observations from a 2x finer mesh)"),
+        "config": config_dict(w),
         "solves_per_s": world * 1e3 / ms,
         "iterations": mixed.get("iters"), "true_relres": mixed.get("relres"), "status": mixed.get("status"),
         "fp64_form": {"s_per_solve": fp64_ms / 1e3, "iterations": fp64.get("iters"),
@@ -517,7 +525,7 @@ def sweep_arm(args):
 
     build.build()
     w = W.mid()
-    cobs = torch.from_numpy(np.loadtxt(OBS_FILE, ndmin=2)).cuda()
+    cobs = torch.from_numpy(np.loadtxt(obs_file(args), ndmin=2)).cuda()
     prob = api.Problem.from_workload(w)
     b, x = prob.zeros(), prob.zeros()
     prob.rhs(cobs, out=b)
@@ -581,6 +589,8 @@ def main():
     ap.add_argument("--levels", type=int, default=64)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--data", choices=["same-mesh", "refined2"], default="same-mesh",
+                    help="observations: same-mesh forward solve (default) or one on a 2x finer mesh")
     args = ap.parse_args()
     if args.kernel == "sweep":
         sweep_arm(args)
