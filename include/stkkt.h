@@ -159,6 +159,23 @@ kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, 
                      ras_precond** out);
 
 /*
+ * ras_setup_shape -- ras_setup with a requested shape of the subdomain solve
+ *   (a tuning and testing hook; the paper has no counterpart).  The shape
+ *   decides how the solve kernel runs, not what it computes: every compiled
+ *   shape applies the same ILU(0) factors.
+ *   shape[0]  points per chunk of a wavefront (FP64: 32, 20, 12; FP32 with 4
+ *             lanes: 56, 40, 24, with 8 lanes: 28, 20, 12; BF16: 80, 48, 16)
+ *   shape[1]  buffers of the factor-copy ring, 2..4
+ *   shape[2]  lanes per point, 4 or 8 (8 in FP32 only)
+ *   shape[3]  1 = local vectors in shared memory, 2 = in global memory
+ *   A 0 in a field leaves that choice to the library (as ras_setup does).
+ *   Errors: ARG when no compiled shape matches or the chosen one does not fit
+ *   the device's shared memory; otherwise those of ras_setup.
+ */
+kkt_status ras_setup_shape(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
+                           const int shape[4], ras_precond** out);
+
+/*
  * ras_info -- sizes of a preconditioner: boxes, points of all extended boxes
  *   (with overlap), stored factor values and bytes per value.  Any output may
  *   be NULL.
@@ -169,16 +186,39 @@ kkt_status ras_info(const ras_precond* m, int* nbox, long long* points, long lon
 /*
  * ras_solve_shape -- how the subdomain solve of a preconditioner runs (chosen
  *   at ras_setup from the boxes' sizes and the device's occupancy): points per
- *   chunk of a wavefront, buffers of its factor-copy ring, and 1 if the local
- *   vectors live in shared memory.  Any output may be NULL.  Reporting only;
- *   the paper has no counterpart.
+ *   chunk of a wavefront, buffers of its factor-copy ring, lanes per point,
+ *   and 1 if the local vectors live in shared memory.  Any output may be
+ *   NULL.  Reporting only; the paper has no counterpart.
  */
-kkt_status ras_solve_shape(const ras_precond* m, int* chunk_points, int* stages, int* smem_vectors);
+kkt_status ras_solve_shape(const ras_precond* m, int* chunk_points, int* stages, int* lanes, int* smem_vectors);
+
+/*
+ * ras_status -- the preconditioner's device status word, read on `stream`
+ *   (synchronises that stream): 0 = fine; 1 = the last factorisation met a
+ *   zero or non-finite pivot (returns ZERO_PIVOT); 2 = a subdomain solve gave
+ *   up waiting for a factor copy after its 2 s limit and left z unwritten
+ *   (returns ERR_CUDA).  ras_apply and ras_apply_static never synchronise, so
+ *   a caller that does not go through gmres_solve reads the outcome of its
+ *   applies here.  The word is cleared by ras_refactor.
+ */
+kkt_status ras_status(ras_precond* m, int* code, void* stream);
+
+/*
+ * ras_selftest_wait -- test hook for the bounded waits (no counterpart in the
+ *   paper): launches one thread that waits, for limit_ms milliseconds
+ *   (0 < limit_ms <= 1000), on an mbarrier that nothing completes, with the
+ *   same bounded wait the subdomain solve uses; the wait gives up, sets the
+ *   status word of m to 2 and the kernel returns.  Nothing is copied; the
+ *   device and the handle stay usable (ras_refactor clears the word).
+ */
+kkt_status ras_selftest_wait(ras_precond* m, double limit_ms, void* stream);
 
 /*
  * ras_apply -- z = sum_ij (R^0_ij)^T M_ij^{-1} R^delta_ij r (restricted prolongation,
- *   Cai-Sarkis form cited in Sec. 3.2); all boxes in one launch.  r, z FP64, must
- *   not overlap.
+ *   Cai-Sarkis form cited in Sec. 3.2); all boxes in one launch.  r, z FP64,
+ *   3*N*(M+1) values each; the two spans must not overlap (ERR_ARG).  Does not
+ *   synchronise; a solve that gave up on a factor copy is reported by
+ *   ras_status (and by gmres_solve).
  */
 kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream);
 
@@ -191,12 +231,16 @@ kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream);
  *   fixed 32 MiB array compiled into the library, which every GPU that loads
  *   the library holds until the process exits.  (The paper has no counterpart;
  *   this is an interface convenience.)
- *   Limit: the padded local vectors of all subdomains must fit in the array,
- *   i.e. 3 * sum over boxes of (lx+2)(ly+2)(lz+2)(lt+2) values of the factor
- *   precision <= 32 MiB; larger handles get KKT_ERR_ARG (use ras_apply).
+ *   Limit: when the solve keeps the local vectors in global memory
+ *   (ras_solve_shape reports smem_vectors = 0), the padded local vectors of
+ *   all subdomains must fit in the array, i.e. 3 * sum over boxes of
+ *   (lx+2)(ly+2)(lz+2)(lt+2) values of the factor precision (FP32 for BF16
+ *   factors) <= 32 MiB; larger handles get KKT_ERR_ARG (use ras_apply).  A
+ *   solve whose local vectors live in shared memory does not touch the array
+ *   and has no limit.
  *   The first call on a device looks the array's device address up
  *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture.  Every call clears the part of the array it uses on
+ *   stream capture.  Every call that uses the array clears the part it uses on
  *   `stream` before the solve.  All calls share the one array, so calls whose
  *   work overlaps on the GPU (other streams, other threads) race: order them.
  */

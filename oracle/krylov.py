@@ -13,7 +13,7 @@ is on the residual 2-norm relative to ||b|| (zero initial guess, as in
 Sec. 4); when the Arnoldi estimate passes the test the true residual
 b - F x is formed and must pass too, otherwise the method restarts.
 
-Pins: tests/test_oracle_krylov.py (agrees with a dense direct solve; n-step
+Pins: tests/test_oracle_schwarz.py (agrees with a dense direct solve; n-step
 termination without restart; the flexible and standard forms agree for a
 fixed preconditioner; iteration counts are non-increasing in restart).
 """

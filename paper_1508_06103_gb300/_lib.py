@@ -48,7 +48,12 @@ SIGNATURES = {
     "ras_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ras_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                            C.POINTER(C.c_int)]),
-    "ras_solve_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ras_setup_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_void_p)]),
+    "ras_solve_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]),
+    "ras_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p]),
+    "ras_selftest_wait": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "coarse_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
     "two_level_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "kkt_launch_count": (C.c_longlong, []),

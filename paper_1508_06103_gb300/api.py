@@ -113,14 +113,24 @@ class Problem:
 class RAS:
     """One-level space-time RAS with ILU(0) subdomain solves (ras_setup)."""
 
-    def __init__(self, prob: Problem, nsub: Sequence[int], overlap: int, factor_prec: int = 64, local: str = "ilu0"):
-        """factor_prec 64, 32 or 16 (BF16 storage); local "ilu0" or "lu" (exact, FP64 only)."""
+    def __init__(self, prob: Problem, nsub: Sequence[int], overlap: int, factor_prec: int = 64, local: str = "ilu0",
+                 shape: Optional[Sequence[int]] = None):
+        """factor_prec 64, 32 or 16 (BF16 storage); local "ilu0" or "lu" (exact, FP64 only).
+
+        shape: None (chosen by the library) or (chunk points, ring buffers, lanes, placement) for
+        ras_setup_shape, placement 1 = local vectors in shared memory, 2 = in global memory, 0 = any.
+        """
         self._lib = _lib.load()
         self.prob = prob
         ns = (C.c_int * 4)(*[int(v) for v in nsub])
         h = C.c_void_p()
         loc = {"ilu0": 0, "lu": 1}[local]
-        check(self._lib.ras_setup(prob.h, ns, int(overlap), loc, int(factor_prec), C.byref(h)), "ras_setup")
+        if shape is None:
+            check(self._lib.ras_setup(prob.h, ns, int(overlap), loc, int(factor_prec), C.byref(h)), "ras_setup")
+        else:
+            sh = (C.c_int * 4)(*[int(v) for v in shape])
+            check(self._lib.ras_setup_shape(prob.h, ns, int(overlap), loc, int(factor_prec), sh, C.byref(h)),
+                  "ras_setup_shape")
         self.h = h
 
     def apply(self, r: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
@@ -144,10 +154,21 @@ class RAS:
         return dict(nbox=nb.value, points=pts.value, factor_values=fv.value, value_bytes=vb.value)
 
     def solve_shape(self):
-        """dict(chunk_points, stages, smem_vectors) of the subdomain solve."""
-        ch, ns, sv = C.c_int(), C.c_int(), C.c_int()
-        check(self._lib.ras_solve_shape(self.h, C.byref(ch), C.byref(ns), C.byref(sv)), "ras_solve_shape")
-        return dict(chunk_points=ch.value, stages=ns.value, smem_vectors=bool(sv.value))
+        """dict(chunk_points, stages, lanes, smem_vectors) of the subdomain solve."""
+        ch, ns, ln, sv = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(self._lib.ras_solve_shape(self.h, C.byref(ch), C.byref(ns), C.byref(ln), C.byref(sv)),
+              "ras_solve_shape")
+        return dict(chunk_points=ch.value, stages=ns.value, lanes=ln.value, smem_vectors=bool(sv.value))
+
+    def status(self, stream=None) -> int:
+        """The device status word (ras_status); raises KktError for 1 (zero pivot) and 2 (copy wait gave up)."""
+        code = C.c_int()
+        check(self._lib.ras_status(self.h, C.byref(code), _stream(stream)), "ras_status")
+        return code.value
+
+    def selftest_wait(self, limit_ms: float, stream=None) -> None:
+        """Run the bounded-wait self-test kernel (ras_selftest_wait)."""
+        check(self._lib.ras_selftest_wait(self.h, float(limit_ms), _stream(stream)), "ras_selftest_wait")
 
     def timing(self, kernel: int = 0):
         """(total ms, launches) since the last reset: kernel 0 subdomain solve, 1 factorisation."""

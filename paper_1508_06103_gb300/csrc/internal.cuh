@@ -28,6 +28,12 @@ void set_error(const std::string& msg);
     if (st_ < 0) return st_;          \
   } while (0)
 
+// True when the spans [a, a + n) and [b, b + n) of doubles share an element.
+inline bool spans_overlap(const double* a, const double* b, long long n) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b, len = (uintptr_t)n * sizeof(double);
+  return pa < pb + len && pb < pa + len;
+}
+
 // Count of kernel launches made by the library (kkt_launch_count).
 extern std::atomic<long long> g_kernel_launches;
 #define KKT_COUNT(n) g_kernel_launches.fetch_add((n), std::memory_order_relaxed)

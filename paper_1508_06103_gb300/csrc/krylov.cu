@@ -253,6 +253,16 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
         Hij(i, j) = t;
       }
       const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      if (den == 0.0) {
+        // F M^{-1} v_j lies in span(v_0 .. v_{j-1}) with a zero rotated
+        // diagonal: the least-squares problem gains nothing from column j,
+        // so the cycle ends on columns 0 .. j-1 and reports a breakdown.
+        ++it;
+        k = j;
+        stop = true;
+        breakdown = true;
+        break;
+      }
       cs[j] = Hij(j, j) / den;
       sn[j] = Hij(j + 1, j) / den;
       Hij(j, j) = den;

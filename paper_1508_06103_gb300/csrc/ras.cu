@@ -109,6 +109,33 @@ const SlotTables& tables() {
 __constant__ int8_t c_dt[kSlots], c_dz[kSlots], c_dy[kSlots], c_dx[kSlots], c_comp[kSlots];
 __constant__ int c_base[3], c_count[3], c_diag[3];
 
+// Constant memory belongs to the device (each device has its own copy of the
+// module), so the tables are uploaded once per device ordinal, under a lock.
+constexpr int kMaxDevices = 64;
+std::mutex g_tables_mu;
+bool g_tables_done[kMaxDevices] = {};
+
+kkt_status upload_slot_tables(const SlotTables& T) {
+  int dev = 0;
+  KKT_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("ras_setup: device ordinal out of range");
+    return KKT_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_tables_mu);
+  if (g_tables_done[dev]) return KKT_OK;
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dt, T.dt, kSlots));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dz, T.dz, kSlots));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dy, T.dy, kSlots));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dx, T.dx, kSlots));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_comp, T.comp, kSlots));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_base, T.base, sizeof(T.base)));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_count, T.count, sizeof(T.count)));
+  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_diag, T.diag, sizeof(T.diag)));
+  g_tables_done[dev] = true;
+  return KKT_OK;
+}
+
 // Checksum of the slot list and chunk block rank of every slot, as the
 // generated factorisation code (factor32.cu, factor64.cu) assumes them.
 #include "ilu_slots.inc"
@@ -233,14 +260,36 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return done != 0;
 }
-// Bounded wait: gives up after `limit` polls and reports it through *failed.
-__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, int* failed) {
-  constexpr long long kLimit = 1LL << 26;
-  for (long long it = 0; !mbar_try_wait(bar, parity); ++it)
-    if (it > kLimit) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on phase `parity` of an mbarrier: gives up after limit_ns
+// nanoseconds of polling, records status 2 in *failed and returns false.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: a block copy takes microseconds
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* failed,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) {
       atomicExch(failed, 2);
-      return;
+      return false;
     }
+  return true;
+}
+
+// Self-test of the bounded wait (ras_selftest_wait): one thread initialises an
+// mbarrier that expects one arrival, which nothing makes, and waits on it for
+// limit_ns; the wait gives up, sets *status = 2 and the kernel returns.  No
+// copy is issued, so nothing is in flight when the CTA exits.
+__global__ void wait_selftest(int* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  mbar_wait(&bar, 0u, status, limit_ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -251,7 +300,7 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned pari
 // With SMEM the box's padded local vector lives in shared memory as well.
 // ---------------------------------------------------------------------------
 constexpr size_t kSmemLimit = 227 * 1024;          // dynamic shared memory of one CTA
-constexpr int kSolveHeader = 2048;   // off[] table (326 ints) and, from byte 1536, the mbarriers
+constexpr int kSolveHeader = 2048;   // off[] table (326 ints); from byte 1536 the mbarriers and the abort word
 constexpr int kMaxStages = 4;        // buffers of the subdomain solve's copy ring
 
 // Row sums of a step, in two phases so that all neighbour gathers of the
@@ -297,6 +346,7 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
   extern __shared__ __align__(128) unsigned char smem[];
   int* off = reinterpret_cast<int*>(smem);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
+  int* abort_at = reinterpret_cast<int*>(smem + 1536 + 8 * kMaxStages);   // block whose wait gave up, or -1
   S* buf0 = reinterpret_cast<S*>(smem + kSolveHeader);   // nstage buffers of bstride values
                                                         // (kLRanks x the largest chunk row stride)
   const BoxDesc bx = boxes[blockIdx.x];
@@ -313,6 +363,7 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
   if (threadIdx.x == 0) {
     for (int b = 0; b < nstage; ++b) mbar_init(&bar[b], 1);
     mbar_fence_init();
+    *abort_at = -1;
   }
   if (SMEM)
     for (long long i = threadIdx.x; i < npad; i += blockDim.x) v[i] = (T)0;
@@ -359,8 +410,8 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
     nxt = ck[chunk_of(min(1, nblk - 1))];
     vq_cur = j < cur.n ? vtab[bx.poff + cur.q0 + j] : 0;
   }
-  // one step of either sweep
-  auto step = [&](int g, auto upper_tag) {
+  // one step of either sweep; false when a copy wait gave up (the CTA stops)
+  auto step = [&](int g, auto upper_tag) -> bool {
     constexpr bool kUpper = decltype(upper_tag)::value;
     const int b = g % nstage;
     if (threadIdx.x == 0 && g + nstage - 1 < nblk) {
@@ -369,7 +420,7 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
     }
     const Chunk nn = ck[chunk_of(min(g + 2, nblk - 1))];
     const int vq_nxt = (g + 1 < nblk && j < nxt.n) ? vtab[bx.poff + nxt.q0 + j] : 0;
-    mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status);
+    if (!mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status)) *abort_at = g;
     const Chunk& c = cur;
     const S* B = buf0 + (size_t)b * bstride;
     const bool act = j < c.n;
@@ -425,10 +476,24 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
     cur = nxt;
     nxt = nn;
     vq_cur = vq_nxt;
+    return *abort_at < 0;
   };
   // forward sweep (unit lower factor), then backward sweep (upper factor)
-  for (int g = 0; g < nch; ++g) step(g, std::false_type{});
-  for (int g = nch; g < nblk; ++g) step(g, std::true_type{});
+  bool ok = true;
+  for (int g = 0; ok && g < nch; ++g) ok = step(g, std::false_type{});
+  for (int g = nch; ok && g < nblk; ++g) ok = step(g, std::true_type{});
+  if (!ok) {
+    // A wait gave up at block gf (status 2 is set): the blocks gf .. gf +
+    // nstage - 1 may still be in flight into this CTA's buffers.  Thread 0
+    // waits for them, again with the time limit, and the CTA returns without
+    // writing z.
+    if (threadIdx.x == 0) {
+      const int gf = *abort_at;
+      for (int q = gf; q < min(gf + nstage, nblk); ++q)
+        mbar_wait(&bar[q % nstage], (unsigned)(q / nstage) & 1u, status);
+    }
+    return;
+  }
   // scatter the owned part: (R^0)^T (otab: the owned points' global indices and offsets)
   for (int q = threadIdx.x; q < bx.nown; q += blockDim.x) {
     const int2 e = otab[bx.ooff + q];
@@ -477,8 +542,14 @@ template <typename T, bool SMEM, int L>
 const void* solve_kernel() {
   return (const void*)ras_solve<T, SMEM, L>;
 }
+// A requested shape (ras_setup_shape): 0 in a field leaves it to the chooser.
+struct ShapeRequest {
+  int ch = 0, nstage = 0, lanes = 0, place = 0;   // place: 1 shared-memory vector, 2 global-memory vector
+};
 template <typename T, int L>
-kkt_status shape_candidates(int nbox, long long max_pad, int nsm, SolveShape* best, long long* best_key) {
+kkt_status shape_candidates(int nbox, long long max_pad, int nsm, const ShapeRequest& req, SolveShape* best,
+                            long long* best_key) {
+  if (req.lanes != 0 && req.lanes != L) return KKT_OK;
   const int cands[3] = {ChunkCfg<T, L>::CH, ChunkCfg<T, L>::CH2, ChunkCfg<T, L>::CH3};
   KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kSmemLimit));
@@ -488,6 +559,9 @@ kkt_status shape_candidates(int nbox, long long max_pad, int nsm, SolveShape* be
     for (int ns = 2; ns <= kMaxStages; ++ns)
       for (int sv = 1; sv >= 0; --sv) {
         const int ch = cands[ci], cp = chunk_stride<T, L>(ch);
+        if ((req.ch && req.ch != ch) || (req.nstage && req.nstage != ns) || (req.place == 1 && !sv) ||
+            (req.place == 2 && sv))
+          continue;
         const size_t sm = solve_smem(cp, ns, sizeof(T), sizeof(typename SolveArith<T>::type), max_pad, sv != 0);
         if (sm > kSmemLimit) continue;
         const int threads = (ch * L + 31) / 32 * 32;
@@ -508,12 +582,18 @@ kkt_status shape_candidates(int nbox, long long max_pad, int nsm, SolveShape* be
       }
   return KKT_OK;
 }
+// Picks the best shape allowed by `req`; KKT_ERR_ARG when none is.
 template <typename T>
-kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, SolveShape* out) {
-  SolveShape best{ChunkCfg<T, 4>::CH, chunk_stride<T, 4>(ChunkCfg<T, 4>::CH), 2, 4, false};
+kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, const ShapeRequest& req, SolveShape* out) {
+  SolveShape best{};
   long long best_key = -1;
-  KKT_TRY((shape_candidates<T, 4>(nbox, max_pad, nsm, &best, &best_key)));
-  if constexpr (LaneSet<T>::N > 1) KKT_TRY((shape_candidates<T, 8>(nbox, max_pad, nsm, &best, &best_key)));
+  KKT_TRY((shape_candidates<T, 4>(nbox, max_pad, nsm, req, &best, &best_key)));
+  if constexpr (LaneSet<T>::N > 1) KKT_TRY((shape_candidates<T, 8>(nbox, max_pad, nsm, req, &best, &best_key)));
+  if (best_key < 0) {
+    set_error("ras_setup: no subdomain-solve shape fits the request (chunk size, ring depth, lanes and vector "
+              "placement must be a compiled combination that fits in shared memory)");
+    return KKT_ERR_ARG;
+  }
   *out = best;
   return KKT_OK;
 }
@@ -521,7 +601,7 @@ kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, SolveShape* 
 }  // namespace
 
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
-                      ras_precond** out) {
+                      const int* shape, ras_precond** out) {
   if (!p || !nsub || !out) {
     set_error("ras_setup: null argument");
     return KKT_ERR_ARG;
@@ -563,18 +643,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     set_error("ras_setup: internal slot table mismatch");
     return KKT_ERR_ARG;
   }
-  static bool consts_done = false;   // constant memory is per module; upload once per process
-  if (!consts_done) {
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dt, T.dt, kSlots));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dz, T.dz, kSlots));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dy, T.dy, kSlots));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dx, T.dx, kSlots));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_comp, T.comp, kSlots));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_base, T.base, sizeof(T.base)));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_count, T.count, sizeof(T.count)));
-    KKT_TRY_CUDA(cudaMemcpyToSymbol(c_diag, T.diag, sizeof(T.diag)));
-    consts_done = true;
-  }
+  KKT_TRY(upload_slot_tables(T));
 
   ras_precond* m = new (std::nothrow) ras_precond();
   if (!m) return KKT_ERR_NOMEM;
@@ -602,10 +671,17 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       return KKT_ERR_CUDA;
     }
     const int nbox = nsub[0] * nsub[1] * nsub[2] * nsub[3];
+    ShapeRequest req;
+    if (shape) {
+      req.ch = shape[0];
+      req.nstage = shape[1];
+      req.lanes = shape[2];
+      req.place = shape[3];
+    }
     SolveShape sh{};
-    const kkt_status cs = factor_prec == 64   ? choose_solve_shape<double>(nbox, pad, nsm, &sh)
-                          : factor_prec == 32 ? choose_solve_shape<float>(nbox, pad, nsm, &sh)
-                                              : choose_solve_shape<__nv_bfloat16>(nbox, pad, nsm, &sh);
+    const kkt_status cs = factor_prec == 64   ? choose_solve_shape<double>(nbox, pad, nsm, req, &sh)
+                          : factor_prec == 32 ? choose_solve_shape<float>(nbox, pad, nsm, req, &sh)
+                                              : choose_solve_shape<__nv_bfloat16>(nbox, pad, nsm, req, &sh);
     if (cs != KKT_OK) {
       delete m;
       return cs;
@@ -905,7 +981,22 @@ kkt_status ras_check(ras_precond* m) {
 
 extern "C" kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
                                 ras_precond** out) {
-  return ras_create(p, nsub, overlap, local, factor_prec, out);
+  return ras_create(p, nsub, overlap, local, factor_prec, nullptr, out);
+}
+
+extern "C" kkt_status ras_setup_shape(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
+                                      const int shape[4], ras_precond** out) {
+  if (!shape) {
+    set_error("ras_setup_shape: null shape");
+    return KKT_ERR_ARG;
+  }
+  if (shape[0] < 0 || shape[1] < 0 || (shape[1] != 0 && (shape[1] < 2 || shape[1] > kMaxStages)) ||
+      (shape[2] != 0 && shape[2] != 4 && shape[2] != 8) || shape[3] < 0 || shape[3] > 2) {
+    set_error("ras_setup_shape: shape = {chunk points >= 0, ring buffers 0 or 2..4, lanes 0, 4 or 8, "
+              "vector placement 0, 1 or 2}");
+    return KKT_ERR_ARG;
+  }
+  return ras_create(p, nsub, overlap, local, factor_prec, shape, out);
 }
 
 extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream) {
@@ -913,21 +1004,55 @@ extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void
     set_error("ras_apply: null argument");
     return KKT_ERR_ARG;
   }
-  if (r == z) {
+  if (spans_overlap(r, z, m->prob->n)) {
     set_error("ras_apply: r and z must not overlap");
     return KKT_ERR_ARG;
   }
   return ras_launch(m, r, z, (cudaStream_t)stream);
 }
 
-extern "C" kkt_status ras_solve_shape(const ras_precond* m, int* chunk_points, int* stages, int* smem_vectors) {
+extern "C" kkt_status ras_solve_shape(const ras_precond* m, int* chunk_points, int* stages, int* lanes,
+                                      int* smem_vectors) {
   if (!m) {
     set_error("ras_solve_shape: null argument");
     return KKT_ERR_ARG;
   }
   if (chunk_points) *chunk_points = m->ch;
   if (stages) *stages = m->nstage;
+  if (lanes) *lanes = m->lanes;
   if (smem_vectors) *smem_vectors = m->smem_vec ? 1 : 0;
+  return KKT_OK;
+}
+
+extern "C" kkt_status ras_status(ras_precond* m, int* code, void* stream) {
+  if (!m || !code) {
+    set_error("ras_status: null argument");
+    return KKT_ERR_ARG;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  int st = 0;
+  KKT_TRY_CUDA(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KKT_TRY_CUDA(cudaStreamSynchronize(s));
+  *code = st;
+  if (*code == 2) {
+    set_error("ras_status: a subdomain solve gave up waiting for its factor copy");
+    return KKT_ERR_CUDA;
+  }
+  if (*code == 1) {
+    set_error("ras_status: zero or non-finite pivot in a subdomain factorisation");
+    return KKT_ERR_ZERO_PIVOT;
+  }
+  return KKT_OK;
+}
+
+extern "C" kkt_status ras_selftest_wait(ras_precond* m, double limit_ms, void* stream) {
+  if (!m || !(limit_ms > 0.0) || limit_ms > 1000.0) {
+    set_error("ras_selftest_wait: null handle or limit_ms outside (0, 1000]");
+    return KKT_ERR_ARG;
+  }
+  wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(m->status, (unsigned long long)(limit_ms * 1e6));
+  KKT_COUNT(1);
+  KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
 }
 
@@ -1038,7 +1163,7 @@ extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* 
     set_error("ras_apply_static: null argument");
     return KKT_ERR_ARG;
   }
-  if (r == z) {
+  if (spans_overlap(r, z, m->prob->n)) {
     set_error("ras_apply_static: r and z must not overlap");
     return KKT_ERR_ARG;
   }
@@ -1046,19 +1171,23 @@ extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* 
     set_error("ras_apply_static: only ILU(0) preconditioners have a static-scratch apply; use ras_apply");
     return KKT_ERR_ARG;
   }
-  const size_t bytes = (size_t)m->vcount * (m->prec == 64 ? sizeof(double) : sizeof(float));
-  if (bytes > kStaticScratchBytes) {
-    set_error("ras_apply_static: the subdomain local vectors need " + std::to_string(bytes) +
-              " bytes, more than the " + std::to_string(kStaticScratchBytes) +
-              "-byte static scratch; use ras_apply");
-    return KKT_ERR_ARG;
-  }
   void* scratch = nullptr;
   KKT_TRY(static_scratch(&scratch));
   cudaStream_t s = (cudaStream_t)stream;
-  // the ghost layers of the local vectors must read zero; earlier calls (on
-  // any handle) may have left other data at those positions
-  KKT_TRY_CUDA(cudaMemsetAsync(scratch, 0, bytes, s));
+  // A solve that keeps the local vectors in shared memory never reads the
+  // scratch: no size limit and nothing to clear.
+  if (!m->smem_vec) {
+    const size_t bytes = (size_t)m->vcount * (m->prec == 64 ? sizeof(double) : sizeof(float));
+    if (bytes > kStaticScratchBytes) {
+      set_error("ras_apply_static: the subdomain local vectors need " + std::to_string(bytes) +
+                " bytes, more than the " + std::to_string(kStaticScratchBytes) +
+                "-byte static scratch; use ras_apply");
+      return KKT_ERR_ARG;
+    }
+    // the ghost layers of the local vectors must read zero; earlier calls (on
+    // any handle) may have left other data at those positions
+    KKT_TRY_CUDA(cudaMemsetAsync(scratch, 0, bytes, s));
+  }
   if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)scratch, s);
   if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)scratch, s);
   return launch_solve<__nv_bfloat16>(m, r, z, (float*)scratch, s);

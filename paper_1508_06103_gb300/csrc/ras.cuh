@@ -80,8 +80,10 @@ struct ras_precond {
   TimingLog factor_timing;     // ILU(0) factorisation launches
 };
 
+// shape: NULL, or {chunk points, ring buffers, lanes per point, vector placement
+// (1 shared, 2 global)} of the subdomain solve, 0 = chosen automatically
 kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
-                      ras_precond** out);
+                      const int* shape, ras_precond** out);
 kkt_status ras_factor(ras_precond* m, cudaStream_t s);          // enqueue, synchronise, check
 kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s);  // enqueue only
 kkt_status ras_factor_status(ras_precond* m);                   // after the stream completed

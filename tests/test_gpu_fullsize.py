@@ -6,6 +6,11 @@
   mixed form with FP32 or BF16-stored factors; the recovered sources of the
   mixed forms, solved to 1e-10, agree with the FP64 form's to 1e-5 relative
   L2 (the accuracy bound stated for the mixed form).
+* The benchmark's fine subdomain solve itself (local vectors in global
+  memory, 4 lanes per point), FP64 and FP32 factors, at 32^3 x 64: z on the
+  owned points of two of its 256 boxes against the oracle's ILU(0) of those
+  boxes (RAS is a disjoint union over the owned sets, so those entries depend
+  on that box alone), with the small-case bars.
 * 8^3 cells x 16 implicit-Euler steps (37,179 unknowns), one-level RAS
   2x2x2x2, overlap 1, exact local LU (and ILU(0)): the GPU solution agrees
   with the oracle's solution of the same system to 1e-8 relative after both
@@ -56,6 +61,38 @@ def _solve(api, w, prob, cobs, prec, rtol):
     x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, coarse=co, restart=w.restart, rtol=rtol, maxit=2000)
     f = prob.recover_source(x).cpu().numpy()
     return x.cpu().numpy(), f, st, its, rel, bd.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def sampled_boxes(mid_setup):
+    """Oracle ILU(0) solves of the corner box and of an interior box of the 4^4 fine split."""
+    w, p, cobs, b, prob = mid_setup
+    r = W.random_vector(prob.n, 21)
+    bxs = osch.boxes(p, w.nsub, w.overlap)
+    interior = 1 + w.nsub[0] * (1 + w.nsub[1] * (1 + w.nsub[2] * 1))
+    refs = []
+    for bi in (0, interior):
+        nodes, levels = osch.box_nodes_levels(p, bxs[bi])
+        A = okkt.assemble_box(p, nodes, levels)
+        idx, owned = osch.box_unknowns(p, bxs[bi])
+        ilu = osch.ILU0(A, osch.local_pattern(p, idx))
+        refs.append((idx[owned], ilu.solve(r[idx])[owned]))
+    return r, refs
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fine_ras_full_size_sampled_boxes_match_oracle(api, mid_setup, sampled_boxes, prec):
+    w, p, cobs, b, prob = mid_setup
+    r, refs = sampled_boxes
+    ras = api.RAS(prob, w.nsub, w.overlap, prec)
+    sh = ras.solve_shape()
+    assert not sh["smem_vectors"] and sh["lanes"] == 4   # the instance the benchmark times
+    z = ras.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    for gi, zr in refs:
+        if prec == 64:
+            assert np.abs(z[gi] - zr).max() <= 1e-9 * np.abs(zr).max()
+        else:
+            assert np.linalg.norm(z[gi] - zr) <= 1e-3 * np.linalg.norm(zr)
 
 
 def test_rhs_full_size_matches_oracle(mid_setup):

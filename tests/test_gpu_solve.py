@@ -106,6 +106,51 @@ def test_exact_lu_rejects_other_precisions_and_static_apply(api):
         ras.apply_static(_dev(W.random_vector(prob.n, 1)))
 
 
+# Every compiled instance of the subdomain solve, as (factor precision, lanes per point,
+# placement of the local vectors: 1 shared memory, 2 global memory, chunk points or 0 = the
+# library's choice).  The 32^3 x 64 benchmark runs (32, 4, 2) on its fine boxes and the FP64
+# form (64, 4, 2); the small boxes of these cases would otherwise always get placement 1.
+INSTANCES = [(64, 4, 1, 0), (64, 4, 2, 0), (64, 4, 2, 12), (32, 4, 1, 0), (32, 4, 2, 0), (32, 4, 2, 24),
+             (32, 8, 1, 0), (32, 8, 2, 0), (16, 4, 1, 0), (16, 4, 2, 0), (16, 4, 2, 16)]
+
+
+def _ras_bar_ok(prec, z, zr):
+    if prec == 64:
+        return np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
+    if prec == 32:
+        return np.linalg.norm(z - zr) <= 1e-3 * np.linalg.norm(zr)
+    return np.linalg.norm(z - zr) <= 8 * 2.0**-8 * np.linalg.norm(zr)
+
+
+@pytest.mark.parametrize("inst", INSTANCES, ids=[f"fp{p}-l{l}-{'smem' if v == 1 else 'gmem'}-ch{c}"
+                                                for p, l, v, c in INSTANCES])
+@pytest.mark.parametrize("case", RAS_CASES, ids=["2x2x1x2", "3x2x2x3-ov2", "single"])
+def test_ras_apply_every_solve_instance_matches_oracle(api, case, inst):
+    prec, lanes, place, ch = inst
+    w = W.random_small(nsens=6, **case["w"])
+    p = okkt.Problem.from_workload(w)
+    ref = osch.RAS(p, okkt.assemble(p), case["nsub"], case["ov"], "ilu0")
+    prob = api.Problem.from_workload(w)
+    ras = api.RAS(prob, case["nsub"], case["ov"], prec, shape=(ch, 0, lanes, place))
+    sh = ras.solve_shape()
+    assert sh["lanes"] == lanes and sh["smem_vectors"] == (place == 1)
+    assert ch == 0 or sh["chunk_points"] == ch
+    for seed in (1, 2):
+        r = W.random_vector(prob.n, seed)
+        z = ras.apply(_dev(r)).cpu().numpy()
+        assert _ras_bar_ok(prec, z, ref.apply(r))
+
+
+def test_setup_shape_rejects_shapes_that_do_not_exist(api):
+    from paper_1508_06103_gb300._lib import KktError
+
+    case = RAS_CASES[0]
+    prob = api.Problem.from_workload(W.random_small(nsens=6, **case["w"]))
+    for prec, shape in ((64, (0, 0, 8, 0)), (32, (33, 0, 0, 0)), (16, (0, 5, 0, 0)), (32, (0, 0, 0, 3))):
+        with pytest.raises(KktError):
+            api.RAS(prob, case["nsub"], case["ov"], prec, shape=shape)
+
+
 def test_solve_shape_is_reported_and_valid(api):
     # the chunk size, copy-ring depth and vector placement chosen at set-up
     case = RAS_CASES[1]
@@ -114,6 +159,7 @@ def test_solve_shape_is_reported_and_valid(api):
     for prec, sizes in ((64, {32, 20, 12}), (32, {56, 40, 24, 28, 20, 12}), (16, {80, 48, 16})):
         sh = api.RAS(prob, case["nsub"], case["ov"], prec).solve_shape()
         assert sh["chunk_points"] in sizes and 2 <= sh["stages"] <= 4 and isinstance(sh["smem_vectors"], bool)
+        assert sh["lanes"] in ((4, 8) if prec == 32 else (4,))
 
 
 def test_ras_apply_fp32_close_to_oracle(api):
@@ -151,15 +197,17 @@ def _two_level_case():
     return W.mid(cells=(4, 4, 4), M=8, nsub=(2, 2, 2, 2), overlap=1, coarse_cells=(2, 2, 2), coarse_M=4)
 
 
+@pytest.mark.parametrize("place", [0, 1, 2], ids=["auto", "fine-smem", "fine-gmem"])
 @pytest.mark.parametrize("reg", ["h1h1", "h1l2"])
-def test_two_level_apply_fp64_matches_oracle(api, reg):
-    # under H1-L2 this also checks that the coarse level takes the fine level's regularisation
+def test_two_level_apply_fp64_matches_oracle(api, reg, place):
+    # under H1-L2 this also checks that the coarse level takes the fine level's regularisation;
+    # `place` forces the fine subdomain solve's local vectors into shared or global memory
     w = dataclasses.replace(_two_level_case(), reg=reg)
     p = okkt.Problem.from_workload(w)
     F = okkt.assemble(p)
     ref = osch.TwoLevel(p, F, w.nsub, w.overlap, w.coarse_cells, w.coarse_M, 1, 0.1, 4, "ilu0")
     prob = api.Problem.from_workload(w)
-    ras = api.RAS(prob, w.nsub, w.overlap, 64)
+    ras = api.RAS(prob, w.nsub, w.overlap, 64, shape=None if place == 0 else (0, 0, 0, place))
     coarse = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, 1, 0.1, 4, 64)
     x = W.random_vector(prob.n, 5)
     z = coarse.apply(ras, _dev(x)).cpu().numpy()

@@ -7,6 +7,13 @@ finer mesh with a smaller time step).
   1x data to the 4x data is about (1 - 1/16) / (1/4 - 1/16) = 5 times that of the 2x data
   (first order would give 3).  This checks that every refinement discretises the same problem
   (coefficients, sensor positions, source, time levels).
+* The noise model of Sec. 4, C^eps = C + eps r C with r standard Gaussian, fixed by what the
+  paper states about it rather than by its formula: the noise is relative (a sensor whose state
+  is zero reads exactly zero, and scaling C scales the data by the same factor for fixed draws),
+  its level is eps (over many samples the relative perturbation (C^eps - C) / (eps C) has mean 0
+  and standard deviation 1, drawn with the workload's own generator), and without noise the data
+  are C at the sensor locations: for a state that is the nodal interpolant of a known function,
+  the function's values at the sensors' (node-snapped) coordinates.
 """
 
 import dataclasses
@@ -56,3 +63,45 @@ def test_iterative_step_solver_matches_sparse_lu():
     a = forward.forward_march(p, f)
     b = forward.forward_march(p, f, solver="bicgstab")
     assert np.abs(a - b).max() <= 1e-11 * np.abs(a).max()
+
+
+def _noise_case():
+    w = W.random_small(6, cells=(4, 3, 3), M=8, nsens=7)
+    p = kkt.Problem.from_workload(w)
+    xyz = w.node_coords()
+    t = np.arange(p.L)[:, None] * p.tau
+    C = np.sin(1.0 + xyz[:, 0])[None, :] * np.cos(0.5 + xyz[:, 1] - xyz[:, 2])[None, :] * (1.0 + t)
+    return w, p, C
+
+
+def test_noise_is_relative_and_of_degree_one_in_the_state():
+    w, p, C = _noise_case()
+    r = np.random.default_rng(3).standard_normal((p.L, len(p.sensor_node)))
+    obs = forward.observations(p, C, r, 0.05)
+    assert np.array_equal(forward.observations(p, np.zeros_like(C), r, 0.05), np.zeros_like(obs))
+    assert np.allclose(forward.observations(p, 3.0 * C, r, 0.05), 3.0 * obs, rtol=1e-15, atol=0)
+    Cz = C.copy()
+    Cz[:, p.sensor_node[0]] = 0.0
+    assert np.all(forward.observations(p, Cz, r, 0.05)[:, 0] == 0.0)
+
+
+def test_noise_level_is_eps_with_the_workloads_own_draws():
+    w = W.random_small(7, cells=(6, 6, 6), M=40, nsens=120)
+    w = dataclasses.replace(w, noise_eps=0.02)
+    p = kkt.Problem.from_workload(w)
+    C = 1.0 + np.abs(W.random_vector(p.L * p.N, 9)).reshape(p.L, p.N)
+    obs = forward.observations(p, C, w.noise(), w.noise_eps)
+    rel = (obs - C[:, p.sensor_node]) / (w.noise_eps * C[:, p.sensor_node])
+    assert rel.size > 4000
+    assert abs(rel.mean()) < 4.0 / np.sqrt(rel.size) and abs(rel.std() - 1.0) < 0.05
+
+
+def test_noise_free_data_are_the_state_at_the_sensor_locations():
+    w, p, C = _noise_case()
+    obs = forward.observations(p, C, np.zeros((p.L, len(p.sensor_node))), 0.0)
+    hx, hy, hz = w.h
+    snapped = np.rint(w.sensor_xyz / np.array([hx, hy, hz])) * np.array([hx, hy, hz])
+    t = np.arange(p.L)[:, None] * p.tau
+    expect = (np.sin(1.0 + snapped[:, 0])[None, :] * np.cos(0.5 + snapped[:, 1] - snapped[:, 2])[None, :]
+              * (1.0 + t))
+    assert np.allclose(obs, expect, rtol=1e-14, atol=1e-14)

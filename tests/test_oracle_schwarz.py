@@ -88,6 +88,32 @@ def test_ras_variants_agree_without_overlap():
     assert np.allclose(a, b, rtol=1e-13, atol=1e-13)
 
 
+def test_restricted_form_takes_owned_values_from_its_own_box_alone():
+    """Pins the RAS operand order at overlap >= 1 (Sec. 3.2; the restricted form of Cai and
+    Sarkis, z = sum (R^0)^T M^{-1} R^delta r).  Owned sets are disjoint, so z on box k's owned
+    points is the owned part of M_k^{-1} (r on k's extended set): it must equal a dense solve of
+    the principal submatrix and must not move when r changes outside the extended set.  The
+    literal order (R^delta)^T M^{-1} R^0 sums, at an owned point, the solves of every box that
+    overlaps it, each fed only its own owned residual, and fails both."""
+    p, F = _small(cells=(4, 3, 3), M=5)
+    nsub = (2, 2, 1, 2)
+    ras = schwarz.RAS(p, F, nsub, 1, "lu")
+    har = schwarz.RAS(p, F, nsub, 1, "lu", variant="harmonic")
+    r = W.random_vector(p.n, 4)
+    for k in (0, len(ras.boxes) - 1):
+        idx, owned = schwarz.box_unknowns(p, ras.boxes[k])
+        outside = np.ones(p.n, dtype=bool)
+        outside[idx] = False
+        r2 = r.copy()
+        r2[outside] += W.random_vector(int(outside.sum()), 5 + k)
+        zo = ras.apply(r)[idx[owned]]
+        zd = np.linalg.solve(F[idx][:, idx].toarray(), r[idx])[owned]
+        assert np.allclose(zo, zd, rtol=1e-9, atol=1e-12 * np.abs(zd).max())
+        assert np.array_equal(zo, ras.apply(r2)[idx[owned]])
+        assert not np.allclose(har.apply(r)[idx[owned]], zd, rtol=1e-3, atol=1e-3 * np.abs(zd).max())
+        assert not np.allclose(har.apply(r)[idx[owned]], har.apply(r2)[idx[owned]])
+
+
 def test_ras_with_overlap_is_a_better_preconditioner():
     p, F = _small(cells=(4, 3, 3), M=5)
     b = W.random_vector(p.n, 2)
