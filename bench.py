@@ -45,6 +45,8 @@ UNIT = "s"
 OBS_FILE = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64.txt")
 # the same observations from a forward solve on a 2x finer mesh (the paper's data protocol)
 OBS_FILE_REFINED = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64_refined2.txt")
+# observations of the 64^3 x 128 workload (same-mesh forward solve)
+OBS_FILE_LARGE = os.path.join(ROOT, "tests", "golden", "observations_large_64x64x64x128.txt")
 
 
 def obs_file(args) -> str:
@@ -192,7 +194,7 @@ def oracle_sample(iterations: int, budget_rows: int = 15000):
 
     fac_f, sol_f, rows_f = box_costs(p, w.nsub, w.overlap, budget_rows)
     pc = schwarz.coarse_problem(p, w.coarse_cells, w.coarse_M)
-    fac_c, sol_c, rows_c = box_costs(pc, w.nsub, w.coarse_overlap, budget_rows // 2)
+    fac_c, sol_c, rows_c = box_costs(pc, w.coarse_split, w.coarse_overlap, budget_rows // 2)
     t = time.time()
     kkt.apply(pc, np.ones(pc.n))
     t_mv_c = time.time() - t
@@ -287,8 +289,8 @@ def gpu_arm(args):
 
     def make(prec):
         ras = api.RAS(prob, w.nsub, w.overlap, prec)
-        co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, w.coarse_overlap, w.coarse_rtol, w.coarse_maxit,
-                        prec)
+        co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.coarse_split, w.coarse_overlap, w.coarse_rtol,
+                        w.coarse_maxit, prec)
         return ras, co
 
     last = {}
@@ -479,7 +481,8 @@ def kernel_arm(args):
     out = {"kernel": args.kernel, "cells": c, "levels": M, "unknowns": prob.n}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.kernel == "ras":
-        ras = api.RAS(prob, w.nsub, w.overlap, args.prec)
+        shape = None if not (args.chunk or args.stages) else (args.chunk, args.stages, 0, 0)
+        ras = api.RAS(prob, w.nsub, w.overlap, args.prec, shape=shape)
         ras.apply(x, y)
         torch.cuda.synchronize()
         e0.record()
@@ -544,7 +547,7 @@ def sweep_arm(args):
         ras = api.RAS(prob, w.nsub, delta, 32)
         co = None
         if levels == 2:
-            co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, w.coarse_overlap, w.coarse_rtol,
+            co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.coarse_split, w.coarse_overlap, w.coarse_rtol,
                             w.coarse_maxit, 32)
         last = {}
 
@@ -574,6 +577,85 @@ def sweep_arm(args):
         ras.close()
 
 
+def large_arm(args):
+    """The 64^3 x 128 single solve (106M unknowns): FP32 subdomain and coarse solves, FP64 FGMRES(40).
+
+    One step = right-hand side, refactorisation of the fine and coarse factors, the FGMRES solve
+    to a true relative residual of 1e-8 and the source extraction, as in the default benchmark.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    build.build()
+    w = W.large()
+    cobs = torch.from_numpy(np.loadtxt(OBS_FILE_LARGE, ndmin=2)).cuda()
+    prob = api.Problem.from_workload(w)
+    b, x = prob.zeros(), prob.zeros()
+    f = torch.empty(prob.levels * prob.N, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_setup = time.time()
+    ras = api.RAS(prob, w.nsub, w.overlap, 32)
+    co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.coarse_split, w.coarse_overlap, w.coarse_rtol,
+                    w.coarse_maxit, 32)
+    setup_s = time.time() - t_setup
+    last = {}
+
+    def step():
+        prob.rhs(cobs, out=b)
+        co.refactor_with(ras)
+        x.zero_()
+        _, st, its, rel = api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=w.restart, rtol=w.rtol,
+                                          maxit=2000)
+        prob.recover_source(x, out=f)
+        last.update(status=st, iterations=its, relres=rel)
+
+    for _ in range(args.warmup):
+        step()
+    api.timing_reset(prob, ras)
+    api.timing_enable(True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = timed(step, args.steps)
+    api.timing_enable(False)
+    ras_ms, ras_n = ras.timing(0)
+    fac_ms, fac_n = ras.timing(1)
+    mv_ms, mv_n = api.matvec_timing(prob)
+    free, total = torch.cuda.mem_get_info()
+    info = ras.info()
+    peak, peak_kind = measured_peaks()
+    solve_bytes = info["points"] * SLOTS_PER_POINT * info["value_bytes"] + info["points"] * 24 + prob.n * 8
+    avg_solve = ras_ms / max(ras_n, 1)
+    out = {
+        "metric": "KKT solve s to 1e-8 rel. residual at 64^3x128 (FP32 subdomain solves, FGMRES(40))",
+        "value": ms / 1e3, "unit": "s", "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "workload": f"{w.name}: {prob.n:,} unknowns, 8^4 subdomains overlap 2, coarse 16^3 x 32 (4^4, overlap 1)",
+        "status": last.get("status"), "iterations": last.get("iterations"), "true_relres": last.get("relres"),
+        "setup_s": setup_s, "box_points": info["points"], "factor_gb": info["factor_values"] * info["value_bytes"] / 1e9,
+        "device_memory_used_gb": (total - free) / 1e9, "device_memory_total_gb": total / 1e9,
+        "kernels": {
+            "ilu0_factor": {"avg_launch_ms": fac_ms / max(fac_n, 1), "launches_per_step": fac_n / args.steps},
+            "ras_solve": {"avg_launch_ms": avg_solve, "launches_per_step": ras_n / args.steps,
+                          "alg_bytes_per_launch": solve_bytes, "achieved_gbs": solve_bytes / avg_solve / 1e6,
+                          "frac": solve_bytes / avg_solve / 1e6 / peak, "peak": peak, "peak_source": peak_kind},
+            "matvec_fp64": {"avg_launch_ms": mv_ms / max(mv_n, 1), "launches_per_step": mv_n / args.steps},
+        },
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,10 +671,16 @@ def main():
     ap.add_argument("--levels", type=int, default=64)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--chunk", type=int, default=0, help="--kernel ras: points per chunk (0: the library's choice)")
+    ap.add_argument("--stages", type=int, default=0, help="--kernel ras: copy-ring buffers (0: the library's choice)")
     ap.add_argument("--data", choices=["same-mesh", "refined2"], default="same-mesh",
                     help="observations: same-mesh forward solve (default) or one on a 2x finer mesh")
+    ap.add_argument("--workload", choices=["mid", "large"], default="mid",
+                    help="large: time the 64^3 x 128 single solve instead of the default benchmark")
     args = ap.parse_args()
-    if args.kernel == "sweep":
+    if args.workload == "large":
+        large_arm(args)
+    elif args.kernel == "sweep":
         sweep_arm(args)
     elif args.kernel:
         kernel_arm(args)

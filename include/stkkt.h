@@ -163,10 +163,10 @@ kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, 
  *   (a tuning and testing hook; the paper has no counterpart).  The shape
  *   decides how the solve kernel runs, not what it computes: every compiled
  *   shape applies the same ILU(0) factors.
- *   shape[0]  points per chunk of a wavefront (FP64: 32, 20, 12; FP32 with 4
- *             lanes: 56, 40, 24, with 8 lanes: 28, 20, 12; BF16: 80, 48, 16)
+ *   shape[0]  points per chunk of a wavefront (FP64: 34, 26, 18; FP32: 52, 36,
+ *             20; BF16: 104, 72, 40)
  *   shape[1]  buffers of the factor-copy ring, 2..4
- *   shape[2]  lanes per point, 4 or 8 (8 in FP32 only)
+ *   shape[2]  lanes per point: 4 (the one compiled)
  *   shape[3]  1 = local vectors in shared memory, 2 = in global memory
  *   A 0 in a field leaves that choice to the library (as ras_setup does).
  *   Errors: ARG when no compiled shape matches or the chosen one does not fit
@@ -233,9 +233,10 @@ kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream);
  *   this is an interface convenience.)
  *   Limit: when the solve keeps the local vectors in global memory
  *   (ras_solve_shape reports smem_vectors = 0), the padded local vectors of
- *   all subdomains must fit in the array, i.e. 3 * sum over boxes of
+ *   all subdomains must fit in the array, i.e. 4 * sum over boxes of
  *   (lx+2)(ly+2)(lz+2)(lt+2) values of the factor precision (FP32 for BF16
- *   factors) <= 32 MiB; larger handles get KKT_ERR_ARG (use ras_apply).  A
+ *   factors; 4 values per padded point) <= 32 MiB; larger handles get
+ *   KKT_ERR_ARG (use ras_apply).  A
  *   solve whose local vectors live in shared memory does not touch the array
  *   and has no limit.
  *   The first call on a device looks the array's device address up

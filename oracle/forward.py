@@ -43,8 +43,10 @@ def _dirichlet_rows(Mat: sp.csr_matrix, D: np.ndarray) -> sp.csr_matrix:
 
 
 def _step_solver(A: sp.csc_matrix, solver: str, rtol: float):
-    """x = A^{-1} r: sparse LU, or (for meshes whose LU fill is too large) BiCGSTAB with a
-    Jacobi preconditioner to relative residual rtol, started from the previous step."""
+    """x = A^{-1} r: sparse LU, or (for meshes whose LU fill is too large) Jacobi-preconditioned
+    BiCGSTAB to relative residual rtol, started from the previous step; where BiCGSTAB breaks
+    down (it can on the layered, 100x-contrast diffusivity), Jacobi-preconditioned GMRES(30)
+    from the same start instead.  All are library routines used as one step."""
     if solver == "lu":
         lu = spla.splu(A)
         return lambda r, x0: lu.solve(r)
@@ -59,21 +61,35 @@ def _step_solver(A: sp.csc_matrix, solver: str, rtol: float):
             return np.zeros_like(r)
         x, info = spla.bicgstab(A, r, x0=x0, rtol=rtol, atol=0.0, M=M, maxiter=5000)
         if info != 0:
-            raise RuntimeError(f"bicgstab did not reach rtol {rtol} (info {info})")
+            x, info = spla.gmres(A, r, x0=x0, rtol=rtol, atol=0.0, M=M, restart=30, maxiter=500)
+        if info != 0:
+            raise RuntimeError(f"the step solve did not reach rtol {rtol} (info {info})")
         return x
     return solve
 
 
+def state_step(p: Problem, solver: str = "lu", rtol: float = 1e-13):
+    """x = (B + theta tau S)^{-1} r with identity rows at the Dirichlet nodes (one state step)."""
+    return _step_solver(_dirichlet_rows(p.B + p.theta * p.tau * p.S, p.dirichlet), solver, rtol)
+
+
+def adjoint_step(p: Problem, solver: str = "lu", rtol: float = 1e-13):
+    """x = (B + theta tau S^T)^{-1} r with identity rows at the Dirichlet nodes (one adjoint step)."""
+    return _step_solver(_dirichlet_rows(p.B + p.theta * p.tau * p.S.T.tocsr(), p.dirichlet), solver, rtol)
+
+
 def forward_march(p: Problem, f: np.ndarray, c0: np.ndarray | None = None,
-                  rhs_extra: np.ndarray | None = None, solver: str = "lu", rtol: float = 1e-13) -> np.ndarray:
+                  rhs_extra: np.ndarray | None = None, solver: str = "lu", rtol: float = 1e-13,
+                  step=None) -> np.ndarray:
     """State C^0..C^M (shape (M+1, N)) for nodal source values f (shape (M+1, N)).
 
     rhs_extra[n] (n >= 1), if given, is added to the right-hand side of step n
     (used by the manufactured-solution tests).  solver "lu" (default) or
-    "bicgstab" (to relative residual rtol per step).
+    "bicgstab" (to relative residual rtol per step); `step` (from state_step)
+    reuses a step solver built once.
     """
     th, tau, D = p.theta, p.tau, p.dirichlet
-    solve = _step_solver(_dirichlet_rows(p.B + th * tau * p.S, D), solver, rtol)
+    solve = step if step is not None else state_step(p, solver, rtol)
     R = (p.B - (1.0 - th) * tau * p.S).tocsr()
     C = np.zeros((p.L, p.N))
     if c0 is not None:
@@ -89,11 +105,12 @@ def forward_march(p: Problem, f: np.ndarray, c0: np.ndarray | None = None,
 
 
 def adjoint_march(p: Problem, C: np.ndarray, c_obs: np.ndarray,
-                  rhs_extra: np.ndarray | None = None) -> np.ndarray:
-    """Adjoint G^0..G^M for state C (M+1, N) and observations c_obs (M+1, s)."""
+                  rhs_extra: np.ndarray | None = None, step=None) -> np.ndarray:
+    """Adjoint G^0..G^M for state C (M+1, N) and observations c_obs (M+1, s); `step`
+    (from adjoint_step) reuses a step solver built once (sparse LU by default)."""
     th, tau, D = p.theta, p.tau, p.dirichlet
     St = p.S.T.tocsr()
-    lhs = spla.splu(_dirichlet_rows(p.B + th * tau * St, D))
+    solve = step if step is not None else adjoint_step(p)
     R = (p.B - (1.0 - th) * tau * St).tocsr()
     s = np.where(D, 0.0, p.s)
     G = np.zeros((p.L, p.N))
@@ -107,7 +124,7 @@ def adjoint_march(p: Problem, C: np.ndarray, c_obs: np.ndarray,
         if rhs_extra is not None:
             r = r + rhs_extra[n]
         r[D] = 0.0
-        G[n] = lhs.solve(r)
+        G[n] = solve(r, G[n + 1])
     return G
 
 

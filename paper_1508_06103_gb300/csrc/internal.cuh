@@ -48,11 +48,33 @@ struct TimingLog {
   void reset();
   ~TimingLog();
 };
+
+// Timing of launches captured into a CUDA graph (an FGMRES cycle): the event
+// pairs are created before the capture, recorded as graph nodes, and read
+// after every replay; each pair is tagged with the outer Arnoldi step whose
+// launches it brackets, so pairs of steps the cycle skipped (after it
+// converged, their kernels return at once) are not counted.
+struct CaptureTiming {
+  struct Entry {
+    TimingLog* log;
+    int step;                // outer step, -1 outside the steps (counted always)
+    cudaEvent_t e0, e1;
+  };
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;   // created before the capture
+  size_t used = 0;
+  std::vector<Entry> entries;
+  int step = -1;             // step being captured
+  void clear();
+  ~CaptureTiming() { clear(); }
+};
+extern thread_local CaptureTiming* g_capture;   // set while this thread captures a cycle
+
 // Records an event pair around the launches issued in its scope when timing is on.
 struct TimedScope {
   TimingLog* log;
   cudaStream_t s;
-  cudaEvent_t e0 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool captured = false;
   TimedScope(TimingLog* l, cudaStream_t st);
   ~TimedScope();
 };
@@ -72,6 +94,41 @@ struct DevProblem {
   const float *S32, *ST32, *B32, *K32;      // FP32 copies
   const unsigned char* dir;                 // [N] 1 on Dirichlet nodes
   const double* sens;                       // [N] sensor counts, 0 on Dirichlet nodes
+  const int* gate;                          // device flag: the kernels return at once when it reads 0
+                                            // (an Arnoldi step after convergence); nullptr = always run
+};
+
+// True when a gated kernel should return without work.
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate != nullptr && *gate == 0; }
+
+// Device state of one (F)GMRES instance: the Givens rotations, residual
+// estimate and stop test run on the device, so a restart cycle needs no host
+// round trip (and can be captured into a CUDA graph).
+enum GmresFlag : int { kGmRunning = 0, kGmConverged = 1, kGmBreakdown = 2, kGmNonFinite = 3, kGmLimit = 4 };
+struct GmresState {
+  double bnorm;            // ||b||
+  double beta;             // residual norm at the start of the cycle
+  double rtol;
+  double est;              // Arnoldi residual estimate / ||b||
+  double inv;              // 1 / the norm the next Arnoldi vector is scaled by
+  double b2, r2;           // squared norms of b and of the residual (dot results)
+  int k;                   // columns of the least-squares problem of the cycle
+  int active;              // gate of the cycle's kernels
+  int ran;                 // gate of the update after the cycle (k > 0)
+  int steps;               // Arnoldi steps executed in this cycle
+  int iters;               // steps of all cycles
+  int maxit;
+  int flag;                // GmresFlag
+  int pad_;
+};
+
+// A captured restart cycle of the outer solver and what it was captured for.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long key[10] = {};
+  long long launches = 0;    // kernel launches per replay
+  CaptureTiming timing;
+  void release();
 };
 
 struct GmresWork {
@@ -82,15 +139,30 @@ struct GmresWork {
   double* Z = nullptr;      // m * n (flexible)
   double* w = nullptr;      // n
   double* r = nullptr;      // n
-  double* hbuf = nullptr;   // device scalars: 2 * (m+2)
+  double* hbuf = nullptr;   // device: h, h2 (m+2 each), y (m), cs, sn (m), g (m+1), H ((m+1) m)
+  GmresState* st = nullptr; // device state
+  GmresState* st_host = nullptr;   // pinned host mirror
   double* part = nullptr;   // partial sums
-  double* hhost = nullptr;  // pinned host mirror
   int nparts = 0;
+  cudaStream_t cap = nullptr;      // stream the outer cycle is captured on
+  CycleGraph graph;
   kkt_status alloc(long long n_, int m_, bool flex);
   void release();
+  double* h() const { return hbuf; }
+  double* h2() const { return hbuf + (m + 2); }
+  double* y() const { return hbuf + 2 * (m + 2); }
+  double* cs() const { return y() + m; }
+  double* sn() const { return cs() + m; }
+  double* g() const { return sn() + m; }
+  double* H() const { return g() + (m + 1); }
+  static size_t doubles(int m_) { return 2 * (size_t)(m_ + 2) + 3 * (size_t)m_ + (m_ + 1) + (size_t)(m_ + 1) * m_; }
 };
 
+// Identity of a handle for the cache of captured graphs (never reused).
+unsigned long long next_handle_uid();
+
 struct kkt_problem {
+  unsigned long long uid = next_handle_uid();
   kkt_grid grid;
   int nx, ny, nz, N, M, L;
   long long P, n;                           // points, unknowns
@@ -112,7 +184,8 @@ struct kkt_problem {
   DevProblem dev() const;
 };
 
-// matvec.cu
+// matvec.cu (kernels return at once while *p.gate reads 0)
+kkt_status matvec_prepare();   // raises the kernels' shared-memory limit on the current device
 kkt_status launch_matvec64(const DevProblem& p, const double* x, double* y, cudaStream_t s);
 kkt_status launch_matvec32(const DevProblem& p, const float* x, float* y, cudaStream_t s);
 kkt_status launch_residual(const DevProblem& p, const double* b, const double* x, double* r, cudaStream_t s);
@@ -127,9 +200,12 @@ kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_
                           kkt_problem** out);
 
 // krylov.cu -- device vector helpers used by the solvers
+// An operator y = A x enqueued on stream s; its kernels return at once while
+// *gate reads 0 (gate nullptr: always run).
 struct Operator {
   virtual ~Operator() = default;
-  virtual kkt_status apply(const double* x, double* y, cudaStream_t s) = 0;
+  virtual kkt_status apply(const double* x, double* y, cudaStream_t s, const int* gate) = 0;
+  virtual unsigned long long uid() const = 0;   // identity for the graph cache
 };
 
 struct GmresResult {
@@ -138,12 +214,17 @@ struct GmresResult {
   kkt_status status = KKT_OK;
 };
 
-// Restarted right-preconditioned (F)GMRES with CGS2 on device vectors.
-// `check_true` = form the true residual to confirm convergence.
+// Restarted right-preconditioned (F)GMRES with CGS2 on device vectors, the
+// Givens rotations and stop test on the device.  The outer form
+// (check_true: stop on the true residual) runs one host round trip per
+// restart cycle, replaying the cycle as a captured CUDA graph when `graph`;
+// the inner form (!check_true, zero guess, one cycle: the coarse solve)
+// only enqueues its kernels, gated by `parent` (the outer step's gate).
 kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, GmresWork& ws, int restart,
                      double rtol, int maxit, bool check_true, bool zero_guess, GmresResult* res,
-                     cudaStream_t s);
+                     cudaStream_t s, const int* parent = nullptr, bool graph = false);
 
-kkt_status vec_copy(double* y, const double* x, long long n, cudaStream_t s);
+kkt_status vec_copy(double* y, const double* x, long long n, cudaStream_t s, const int* gate = nullptr);
 kkt_status vec_zero(double* y, long long n, cudaStream_t s);
-kkt_status vec_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s);
+kkt_status vec_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s,
+                     const int* gate = nullptr);

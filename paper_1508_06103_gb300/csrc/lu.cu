@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kLuThreads) lu_step(const BoxDesc* __restrict_
 __global__ void __launch_bounds__(kLuThreads) lu_solve(const BoxDesc* __restrict__ boxes,
                                                        const double* __restrict__ AB, const int* __restrict__ ipiv,
                                                        const double* __restrict__ r, double* __restrict__ z, int nx,
-                                                       int ny, int N) {
+                                                       int ny, int N, const int* gate) {
+  if (gated_off(gate)) return;
   extern __shared__ __align__(16) double bvec[];
   const BoxDesc bx = boxes[blockIdx.x];
   const int n = 3 * (int)bx.P, kl = bx.kl;
@@ -219,6 +220,10 @@ kkt_status ras_lu_factor(ras_precond* m, cudaStream_t s) {
     pmax = std::max(pmax, b.P);
     nmax = std::max(nmax, 3 * (int)b.P);
   }
+  // the solve keeps a box's vector in shared memory (at most kMaxLuUnknowns values); the
+  // limit is raised here, at set-up, so the solve's launch needs no attribute call
+  KKT_TRY_CUDA(cudaFuncSetAttribute(lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kMaxLuUnknowns * sizeof(double))));
   KKT_TRY_CUDA(cudaMemsetAsync(m->AB, 0, m->ab_count * sizeof(double), s));
   KKT_TRY_CUDA(cudaMemsetAsync(m->lu_ju, 0, 2 * m->nbox * sizeof(int), s));
   const dim3 g((unsigned)((pmax + kLuGather - 1) / kLuGather), m->nbox);
@@ -234,13 +239,12 @@ kkt_status ras_lu_factor(ras_precond* m, cudaStream_t s) {
   return KKT_OK;
 }
 
-kkt_status ras_lu_solve(ras_precond* m, const double* r, double* z, cudaStream_t s) {
+kkt_status ras_lu_solve(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate) {
   const kkt_problem* p = m->prob;
   int nmax = 0;
   for (const BoxDesc& b : m->boxes_h) nmax = std::max(nmax, 3 * (int)b.P);
   const size_t smem = (size_t)nmax * sizeof(double);
-  KKT_TRY_CUDA(cudaFuncSetAttribute(lu_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  lu_solve<<<m->nbox, kLuThreads, smem, s>>>(m->boxes, m->AB, m->ipiv, r, z, p->nx, p->ny, p->N);
+  lu_solve<<<m->nbox, kLuThreads, smem, s>>>(m->boxes, m->AB, m->ipiv, r, z, p->nx, p->ny, p->N, gate);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T
                                                            T* __restrict__ y, const double* __restrict__ b,
                                                            int tiles_x, int tiles_y, Axis1D<T> ax, Axis1D<T> ay,
                                                            Axis1D<T> az, LevelW<T> W) {
+  if (gated_off(p.gate)) return;
   extern __shared__ __align__(16) unsigned char mv_sm[];
   T* Xs = reinterpret_cast<T*>(mv_sm);   // [4 slots][3 components][NH]
   T* U = Xs + 4 * 3 * NH;                // [6][NH]
@@ -316,31 +317,45 @@ void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaSt
   az.init(p.nz, p.hz);
   LevelW<T> w;
   w.init(p.tau, p.theta, p.beta1, p.beta2);
-  if (p.reg != 0) {
-    cudaFuncSetAttribute(matvec_tiled<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T>());
+  // (the dynamic shared-memory limits are raised once, in matvec_prepare)
+  if (p.reg != 0)
     matvec_tiled<T, true><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
-  } else {
-    cudaFuncSetAttribute(matvec_tiled<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T>());
+  else
     matvec_tiled<T, false><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
-  }
 }
 
-__global__ void d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {
+__global__ void d2f(const double* __restrict__ x, float* __restrict__ y, long long n, const int* gate) {
+  if (gated_off(gate)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
 
-__global__ void f2d(const float* __restrict__ x, double* __restrict__ y, long long n) {
+__global__ void f2d(const float* __restrict__ x, double* __restrict__ y, long long n, const int* gate) {
+  if (gated_off(gate)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
 
-__global__ void sub_f2d(const double* __restrict__ b, const float* __restrict__ y, double* __restrict__ r, long long n) {
+__global__ void sub_f2d(const double* __restrict__ b, const float* __restrict__ y, double* __restrict__ r, long long n,
+                        const int* gate) {
+  if (gated_off(gate)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     r[i] = b[i] - (double)y[i];
 }
 
 }  // namespace
+
+kkt_status matvec_prepare() {
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mv_smem<double>()));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mv_smem<double>()));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mv_smem<float>()));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mv_smem<float>()));
+  return KKT_OK;
+}
 
 kkt_status launch_matvec64(const DevProblem& p, const double* x, double* y, cudaStream_t s) {
   launch_tiled<double>(p, x, y, nullptr, s);
@@ -367,9 +382,9 @@ kkt_status launch_residual(const DevProblem& p, const double* b, const double* x
 kkt_status launch_residual32(const DevProblem& p, const double* b, const double* x, double* r, float* x32,
                              float* y32, cudaStream_t s) {
   const long long n = 3 * p.P;
-  d2f<<<1216, 256, 0, s>>>(x, x32, n);
+  d2f<<<1216, 256, 0, s>>>(x, x32, n, p.gate);
   launch_tiled<float>(p, x32, y32, nullptr, s);
-  sub_f2d<<<1216, 256, 0, s>>>(b, y32, r, n);
+  sub_f2d<<<1216, 256, 0, s>>>(b, y32, r, n, p.gate);
   KKT_COUNT(3);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
@@ -379,9 +394,9 @@ kkt_status launch_residual32(const DevProblem& p, const double* b, const double*
 kkt_status launch_matvec32_d(const DevProblem& p, const double* x, double* y, float* x32, float* y32,
                              cudaStream_t s) {
   const long long n = 3 * p.P;
-  d2f<<<1216, 256, 0, s>>>(x, x32, n);
+  d2f<<<1216, 256, 0, s>>>(x, x32, n, p.gate);
   launch_tiled<float>(p, x32, y32, nullptr, s);
-  f2d<<<1216, 256, 0, s>>>(y32, y, n);
+  f2d<<<1216, 256, 0, s>>>(y32, y, n, p.gate);
   KKT_COUNT(3);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;

@@ -53,19 +53,42 @@ TimingLog::~TimingLog() {
 }
 
 TimedScope::TimedScope(TimingLog* l, cudaStream_t st) : log(l), s(st) {
-  if (g_timing_on.load() && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
+  if (!g_timing_on.load()) return;
+  if (g_capture) {
+    // inside a graph capture: a pair made before the capture, read after each replay
+    if (g_capture->used < g_capture->pool.size()) {
+      const auto& pr = g_capture->pool[g_capture->used++];
+      e0 = pr.first;
+      e1 = pr.second;
+      captured = true;
+      // an external record becomes an event-record node of the graph (a plain
+      // record in a capturing stream only orders the capture)
+      cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+    }
+    return;
+  }
+  if (cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
   else e0 = nullptr;
 }
 
 TimedScope::~TimedScope() {
   if (!e0) return;
-  cudaEvent_t e1;
+  if (captured) {
+    cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    if (g_capture) g_capture->entries.push_back({log, g_capture->step, e0, e1});
+    return;
+  }
   if (cudaEventCreate(&e1) == cudaSuccess) {
     cudaEventRecord(e1, s);
     log->pending.emplace_back(e0, e1);
   } else {
     cudaEventDestroy(e0);
   }
+}
+
+unsigned long long next_handle_uid() {
+  static std::atomic<unsigned long long> next{1};
+  return next.fetch_add(1);
 }
 
 extern "C" long long kkt_launch_count(void) { return g_kernel_launches.load(); }
@@ -97,6 +120,7 @@ DevProblem kkt_problem::dev() const {
   d.S32 = coef32; d.ST32 = coef32 + c; d.B32 = coef32 + 2 * c; d.K32 = coef32 + 3 * c;
   d.dir = dir;
   d.sens = sens;
+  d.gate = nullptr;
   return d;
 }
 
@@ -297,6 +321,10 @@ kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_
   if (e != cudaSuccess) {
     set_error(std::string("kkt_create: ") + cudaGetErrorString(e));
     return fail(KKT_ERR_CUDA);
+  }
+  {
+    const kkt_status ms = matvec_prepare();
+    if (ms != KKT_OK) return fail(ms);
   }
   *out = p;
   return KKT_OK;

@@ -106,36 +106,6 @@ const SlotTables& tables() {
   return T;
 }
 
-__constant__ int8_t c_dt[kSlots], c_dz[kSlots], c_dy[kSlots], c_dx[kSlots], c_comp[kSlots];
-__constant__ int c_base[3], c_count[3], c_diag[3];
-
-// Constant memory belongs to the device (each device has its own copy of the
-// module), so the tables are uploaded once per device ordinal, under a lock.
-constexpr int kMaxDevices = 64;
-std::mutex g_tables_mu;
-bool g_tables_done[kMaxDevices] = {};
-
-kkt_status upload_slot_tables(const SlotTables& T) {
-  int dev = 0;
-  KKT_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("ras_setup: device ordinal out of range");
-    return KKT_ERR_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_tables_mu);
-  if (g_tables_done[dev]) return KKT_OK;
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dt, T.dt, kSlots));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dz, T.dz, kSlots));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dy, T.dy, kSlots));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_dx, T.dx, kSlots));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_comp, T.comp, kSlots));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_base, T.base, sizeof(T.base)));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_count, T.count, sizeof(T.count)));
-  KKT_TRY_CUDA(cudaMemcpyToSymbol(c_diag, T.diag, sizeof(T.diag)));
-  g_tables_done[dev] = true;
-  return KKT_OK;
-}
-
 // Checksum of the slot list and chunk block rank of every slot, as the
 // generated factorisation code (factor32.cu, factor64.cu) assumes them.
 #include "ilu_slots.inc"
@@ -159,41 +129,36 @@ int slot_rank(int s) {
   return kLRanks + 70 + (s - kFDiag);
 }
 
-// Chunk configurations of the subdomain solve, per stored type S and lanes
-// per point L: candidate chunk sizes (points) and the row-stride rule
-// cp = R (mod Q) that makes the L-lane shared-memory reads of a chunk block
-// free of bank conflicts (the lanes of a warp cover 32/L points and L rows).
-template <typename S, int L>
-struct ChunkCfg;
-template <>
-struct ChunkCfg<float, 4> {
-  static constexpr int CH = 56, CH2 = 40, CH3 = 24;   // 7 / 5 / 3 full warps
-  static constexpr int Q = 16, R = 8;                  // cp = 8 (mod 16)
-};
-template <>
-struct ChunkCfg<float, 8> {
-  static constexpr int CH = 28, CH2 = 20, CH3 = 12;   // 7 / 5 / 3 full warps
-  static constexpr int Q = 8, R = 4;                   // cp = 4 (mod 8)
-};
-template <>
-struct ChunkCfg<double, 4> {
-  static constexpr int CH = 32, CH2 = 20, CH3 = 12;
-  static constexpr int Q = 8, R = 4;                   // cp = 4 (mod 8)
-};
-template <>
-struct ChunkCfg<__nv_bfloat16, 4> {                   // FP32 factors stored as BF16
-  static constexpr int CH = 80, CH2 = 48, CH3 = 16;
-  static constexpr int Q = 32, R = 16;                 // cp = 16 (mod 32): two values per bank word
-};
-// lanes-per-point variants compiled for each stored type
+// Chunk configurations of the subdomain solve, per stored type S: candidate
+// chunk sizes (points) and the row-stride rule cp = R (mod Q) of a chunk
+// block.  In a step the 4 lanes of a point take the stencil neighbours
+// q = lane + 4 i; the factor entries of neighbour q in the C and f rows sit
+// in block rows a + 2q (+1), so the 4 lanes of a point read rows 2 apart and
+// the 8 points of a warp read 8 consecutive columns: with 2 cp = 8 (mod 32)
+// 4-byte words the 32 reads of a warp fall in 32 different banks (for 8-byte
+// values every half warp does; for 2-byte values, two per word).  cp is also
+// a multiple of 16 bytes' worth of values over the 175 and 151 block rows,
+// so every bulk copy starts and ends on 16-byte boundaries.
 template <typename S>
-struct LaneSet {
-  static constexpr int N = 1;   // 4 lanes
+struct ChunkCfg;
+// The chunk sizes are strides the rule allows, so a full chunk carries no
+// padding columns.
+template <>
+struct ChunkCfg<float> {
+  static constexpr int CH = 52, CH2 = 36, CH3 = 20;
+  static constexpr int Q = 16, R = 4;                  // cp = 4 (mod 16)
 };
 template <>
-struct LaneSet<float> {
-  static constexpr int N = 2;   // 4 and 8 lanes
+struct ChunkCfg<double> {
+  static constexpr int CH = 34, CH2 = 26, CH3 = 18;
+  static constexpr int Q = 8, R = 2;                   // cp = 2 (mod 8)
 };
+template <>
+struct ChunkCfg<__nv_bfloat16> {                      // FP32 factors stored as BF16
+  static constexpr int CH = 104, CH2 = 72, CH3 = 40;
+  static constexpr int Q = 32, R = 8;                  // cp = 8 (mod 32): two values per bank word
+};
+constexpr int kLanes = 4;   // lanes per point of the subdomain solve
 // arithmetic type of the solve for a storage type (BF16 factors: FP32)
 template <typename S>
 struct SolveArith {
@@ -212,15 +177,15 @@ __device__ __forceinline__ float arith<float, __nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
 
-template <typename S, int L>
+template <typename S>
 int chunk_stride(int n) {
-  const int Q = ChunkCfg<S, L>::Q, R = ChunkCfg<S, L>::R;
+  const int Q = ChunkCfg<S>::Q, R = ChunkCfg<S>::R;
   return n <= R ? R : R + ((n - R + Q - 1) / Q) * Q;
 }
-int chunk_stride_of(int prec, int lanes, int n) {
-  if (prec == 64) return chunk_stride<double, 4>(n);
-  if (prec == 16) return chunk_stride<__nv_bfloat16, 4>(n);
-  return lanes == 8 ? chunk_stride<float, 8>(n) : chunk_stride<float, 4>(n);
+int chunk_stride_of(int prec, int n) {
+  if (prec == 64) return chunk_stride<double>(n);
+  if (prec == 16) return chunk_stride<__nv_bfloat16>(n);
+  return chunk_stride<float>(n);
 }
 
 // ---------------------------------------------------------------------------
@@ -270,14 +235,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: a block copy takes microseconds
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* failed,
                                           unsigned long long limit_ns = kWaitLimitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > limit_ns) {
-      atomicExch(failed, 2);
-      return false;
+  // the timer is read only every 64 polls, so a copy that lands within the
+  // first polls is seen without the timer's latency
+  unsigned long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u) {
+      const unsigned long long t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > limit_ns) {
+        atomicExch(failed, 2);
+        return false;
+      }
     }
-  return true;
+  }
 }
 
 // Self-test of the bounded wait (ras_selftest_wait): one thread initialises an
@@ -294,57 +266,73 @@ __global__ void wait_selftest(int* status, unsigned long long limit_ns) {
 
 // ---------------------------------------------------------------------------
 // Subdomain solve z = sum_boxes (R^0)^T M^{-1} R^delta r: one CTA per box,
-// LANES lanes per point, one chunk of points per step.  Each lane takes every
-// LANES-th row of the chunk's block in shared memory; the loops have
-// compile-time trip counts and a shuffle reduction closes each row.
-// With SMEM the box's padded local vector lives in shared memory as well.
+// 4 lanes per point, one chunk of points per step.
+//
+// The box's padded local vector holds 4 values per point (C, G, f and a zero),
+// so one 16-byte load fetches a neighbour's three unknowns.  Every L-slot of
+// the three rows of a point reads one of 40 earlier stencil neighbours (27 at
+// level n-1, 13 earlier ones at level n) and every U-slot one of 40 later
+// ones (13 at level n, 27 at n+1), besides the point itself.  Lane l takes
+// the neighbours q = l + 4 i (i < 10) of both sweeps; it loads their values
+// once and forms its parts of the C, G and f row sums from the block rows of
+// those slots, which are affine in q (rows counted within the L or U block):
+//   forward  C row: 2q + c (c: C, f)   G row: 80 + q - 27 (q >= 27)   f row: 94 + 2q + c (c: G, f)
+//   backward C row: 2 + 2q + c (q < 13)   f row: 71 + 2q + c
+//            G row: 29 + q (q < 13), 42 + d + (d >= 13) with d = q - 13; the C entry at
+//            (n+1, same node), q = 26, in row 55
+// and a shuffle reduction over the 4 lanes closes each sum.
 // ---------------------------------------------------------------------------
 constexpr size_t kSmemLimit = 227 * 1024;          // dynamic shared memory of one CTA
-constexpr int kSolveHeader = 2048;   // off[] table (326 ints); from byte 1536 the mbarriers and the abort word
+constexpr int kSolveHeader = 2048;   // from byte 1536: the mbarriers and the abort word
 constexpr int kMaxStages = 4;        // buffers of the subdomain solve's copy ring
+constexpr int kNbr = 40;             // earlier (and later) stencil neighbours of a point
+constexpr int kNbrPerLane = kNbr / kLanes;
+constexpr int kVecWidth = 4;         // values per point in the local vectors
 
-// Row sums of a step, in two phases so that all neighbour gathers of the
-// step are issued before the first multiply-add uses one:
-//   gather<R0, R1, SOFF, L>  loads vp[off[r + SOFF]] for the lane's rows of [R0, R1)
-//   row_sum<R0, R1, L>       sum of B[r*cp + j] * value over those rows, reduced over the L lanes
-template <int R0, int R1, int L>
-struct RowSet {
-  static constexpr int K = (R1 - R0 + L - 1) / L;
-};
-template <int R0, int R1, int SOFF, int L, typename T>
-__device__ __forceinline__ void gather(T (&vals)[RowSet<R0, R1, L>::K], const int* __restrict__ off, const T* vp,
-                                       int lane, bool act) {
-#pragma unroll
-  for (int k = 0; k < RowSet<R0, R1, L>::K; ++k) {
-    const int r = R0 + lane + k * L;
-    vals[k] = (act && r < R1) ? vp[off[r + SOFF]] : (T)0;
-  }
+// the three unknowns of a local-vector point (4 values, 16- or 32-byte aligned)
+__device__ __forceinline__ void ld3(const float* p, float& a, float& b, float& c) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x;
+  b = v.y;
+  c = v.z;
 }
-template <int R0, int R1, int L, typename S, typename T>
-__device__ __forceinline__ T row_sum(const T (&vals)[RowSet<R0, R1, L>::K], const S* __restrict__ B, int cp, int j,
-                                     int lane) {
-  T acc = 0;
+__device__ __forceinline__ void ld3(const double* p, double& a, double& b, double& c) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p);
+  a = v0.x;
+  b = v0.y;
+  c = p[2];
+}
+__device__ __forceinline__ void st3(float* p, float a, float b, float c) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, 0.f);
+}
+__device__ __forceinline__ void st3(double* p, double a, double b, double c) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(c, 0.0);
+}
+
+template <typename T>
+__device__ __forceinline__ T lane_sum(T v) {
 #pragma unroll
-  for (int k = 0; k < RowSet<R0, R1, L>::K; ++k) {
-    const int r = R0 + lane + k * L;
-    if (r < R1) acc += arith<T>(B[r * cp + j]) * vals[k];
-  }
-#pragma unroll
-  for (int o = 1; o < L; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
+  for (int o = 1; o < kLanes; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // S: type of the stored factor values; T: arithmetic and local-vector type
-template <typename S, bool SMEM, int kL>
-__global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
-    const BoxDesc* __restrict__ boxes, const int* __restrict__ perm, const Chunk* __restrict__ chunks,
-    const S* __restrict__ F, typename SolveArith<S>::type* __restrict__ V, const double* __restrict__ r,
-    double* __restrict__ z, const int2* __restrict__ gtab, const int2* __restrict__ otab,
-    const int* __restrict__ vtab, int bstride, int nstage, int* __restrict__ status) {
+// threads of a CTA: the lanes of the largest chunk, in whole warps
+template <typename S>
+constexpr int solve_threads_max() {
+  return (ChunkCfg<S>::CH * kLanes + 31) / 32 * 32;
+}
+
+template <typename S, bool SMEM>
+__global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
+    const BoxDesc* __restrict__ boxes, const Chunk* __restrict__ chunks, const S* __restrict__ F,
+    typename SolveArith<S>::type* __restrict__ V, const double* __restrict__ r, double* __restrict__ z,
+    const int2* __restrict__ gtab, const int2* __restrict__ otab, const int* __restrict__ vtab, int bstride,
+    int nstage, int* __restrict__ status, const int* gate) {
   using T = typename SolveArith<S>::type;
-  static_assert(kL == 4 || kL == 8, "lanes per point");
+  if (gated_off(gate)) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  int* off = reinterpret_cast<int*>(smem);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
   int* abort_at = reinterpret_cast<int*>(smem + 1536 + 8 * kMaxStages);   // block whose wait gave up, or -1
   S* buf0 = reinterpret_cast<S*>(smem + kSolveHeader);   // nstage buffers of bstride values
@@ -354,12 +342,23 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
   const S* Fb = F + bx.foff;
   const int px = bx.lx + 2, py = bx.ly + 2, pz = bx.lz + 2;
   const long long sy = px, sz = (long long)px * py, st = (long long)px * py * pz;
-  const long long npad = 3 * st * (bx.lt + 2);
+  const long long npad = kVecWidth * st * (bx.lt + 2);
   T* v = SMEM ? reinterpret_cast<T*>(buf0 + (size_t)nstage * bstride) : V + bx.voff;
   const int nch = bx.cend - bx.cbeg;
   const Chunk* ck = chunks + bx.cbeg;
-  for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
-    off[s] = (int)(3 * (c_dx[s] + sy * c_dy[s] + sz * c_dz[s] + st * c_dt[s]) + c_comp[s]);
+  const int lane = threadIdx.x & (kLanes - 1), j = threadIdx.x / kLanes;
+  // offsets of the lane's neighbours in the padded local vector
+  int offL[kNbrPerLane], offU[kNbrPerLane];
+#pragma unroll
+  for (int i = 0; i < kNbrPerLane; ++i) {
+    const int q = lane + kLanes * i;
+    // earlier neighbour q: level n-1, spatial offset d = q (q < 27); level n, d = q - 27
+    const int dl = q < 27 ? q : q - 27, tl = q < 27 ? -1 : 0;
+    // later neighbour q: level n, d = 14 + q (q < 13); level n+1, d = q - 13
+    const int du = q < 13 ? 14 + q : q - 13, tu = q < 13 ? 0 : 1;
+    offL[i] = (int)(kVecWidth * ((dl % 3 - 1) + sy * ((dl / 3) % 3 - 1) + sz * (dl / 9 - 1) + st * tl));
+    offU[i] = (int)(kVecWidth * ((du % 3 - 1) + sy * ((du / 3) % 3 - 1) + sz * (du / 9 - 1) + st * tu));
+  }
   if (threadIdx.x == 0) {
     for (int b = 0; b < nstage; ++b) mbar_init(&bar[b], 1);
     mbar_fence_init();
@@ -392,12 +391,9 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
   // (gtab: per box point, its global unknown index and its padded offset)
   for (int q = threadIdx.x; q < (int)P; q += blockDim.x) {
     const int2 e = gtab[bx.poff + q];
-    v[e.y] = (T)r[e.x];
-    v[e.y + 1] = (T)r[e.x + 1];
-    v[e.y + 2] = (T)r[e.x + 2];
+    st3(v + e.y, (T)r[e.x], (T)r[e.x + 1], (T)r[e.x + 2]);
   }
   __syncthreads();
-  const int lane = threadIdx.x & (kL - 1), j = threadIdx.x / kL;
   // Step g works on the chunk of block g (`cur`).  The descriptor of the
   // chunk after next and the point index of the next chunk are loaded one
   // step ahead, so the only loads left between a barrier and the arithmetic
@@ -420,56 +416,71 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
     }
     const Chunk nn = ck[chunk_of(min(g + 2, nblk - 1))];
     const int vq_nxt = (g + 1 < nblk && j < nxt.n) ? vtab[bx.poff + nxt.q0 + j] : 0;
-    if (!mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status)) *abort_at = g;
     const Chunk& c = cur;
-    const S* B = buf0 + (size_t)b * bstride;
     const bool act = j < c.n;
-    T* vp = v;
+    const int cp = c.cp;
+    T* vp = v + (act ? vq_cur : 0);
+    // all neighbour loads of the step first (they depend on the previous steps
+    // only, so they are in flight while the factor block is awaited), then the
+    // arithmetic
+    T nc[kNbrPerLane], ng[kNbrPerLane], nf[kNbrPerLane];
     T v0 = 0, v1 = 0, v2 = 0;
-    if (act) {
-      vp = v + vq_cur;
-      v0 = vp[0];
-      v1 = vp[1];
-      v2 = vp[2];
+#pragma unroll
+    for (int i = 0; i < kNbrPerLane; ++i) {
+      nc[i] = ng[i] = nf[i] = (T)0;
+      if (act) ld3(vp + (kUpper ? offU[i] : offL[i]), nc[i], ng[i], nf[i]);
     }
+    if (act) ld3(vp, v0, v1, v2);
+    if (!mbar_wait(&bar[b], (unsigned)(g / nstage) & 1u, status)) *abort_at = g;
+    const S* B = buf0 + (size_t)b * bstride;
+    T sc = 0, sg = 0, sf = 0;
     if constexpr (!kUpper) {
-      // Every L-slot reads a point of an earlier wavefront except the G row's
-      // own-C slot (block row 93) and the f row's own-G slot (row 174), so the
-      // three rows' sums over other points are gathered together and the two
-      // own-point terms are applied afterwards in C, G, f order.
-      T gC[RowSet<0, 80, kL>::K], gG[RowSet<80, 93, kL>::K], gF[RowSet<94, 174, kL>::K];
-      gather<0, 80, 0, kL>(gC, off, vp, lane, act);
-      gather<80, 93, 28, kL>(gG, off, vp, lane, act);
-      gather<94, 174, 70, kL>(gF, off, vp, lane, act);
-      const T aC = row_sum<0, 80, kL>(gC, B, c.cp, j, lane);
-      const T aG = row_sum<80, 93, kL>(gG, B, c.cp, j, lane);
-      const T aF = row_sum<94, 174, kL>(gF, B, c.cp, j, lane);
+#pragma unroll
+      for (int i = 0; i < kNbrPerLane; ++i) {
+        const int q = lane + kLanes * i;
+        const S* rc = B + (2 * q) * cp + j;
+        const S* rf = B + (94 + 2 * q) * cp + j;
+        sc += arith<T>(rc[0]) * nc[i] + arith<T>(rc[cp]) * nf[i];
+        sf += arith<T>(rf[0]) * ng[i] + arith<T>(rf[cp]) * nf[i];
+        if (q >= 27) sg += arith<T>(B[(80 + q - 27) * cp + j]) * ng[i];
+      }
+      sc = lane_sum(sc);
+      sg = lane_sum(sg);
+      sf = lane_sum(sf);
+      // own-point terms in C, G, f order: the G row's own-C slot (row 93) and
+      // the f row's own-G slot (row 174)
       if (act && lane == 0) {
-        const T yc = v0 - aC;
-        const T yg = v1 - aG - arith<T>(B[93 * c.cp + j]) * yc;
-        const T yf = v2 - aF - arith<T>(B[174 * c.cp + j]) * yg;
-        vp[0] = yc;
-        vp[1] = yg;
-        vp[2] = yf;
+        const T yc = v0 - sc;
+        const T yg = v1 - sg - arith<T>(B[93 * cp + j]) * yc;
+        const T yf = v2 - sf - arith<T>(B[174 * cp + j]) * yg;
+        st3(vp, yc, yg, yf);
       }
     } else {
-      // Every U-slot reads a point of a later wavefront except the C row's
-      // own-f slot (U block row 1), applied after the f row is solved.  The
-      // diagonal rows 0, 28, 70 hold the reciprocals of the pivots.
-      T gF[RowSet<71, 151, kL>::K], gG[RowSet<29, 70, kL>::K], gC[RowSet<2, 28, kL>::K];
-      gather<71, 151, 175, kL>(gF, off, vp, lane, act);
-      gather<29, 70, 94, kL>(gG, off, vp, lane, act);
-      gather<2, 28, 80, kL>(gC, off, vp, lane, act);
-      const T bF = row_sum<71, 151, kL>(gF, B, c.cp, j, lane);
-      const T bG = row_sum<29, 70, kL>(gG, B, c.cp, j, lane);
-      const T bC = row_sum<2, 28, kL>(gC, B, c.cp, j, lane);
+#pragma unroll
+      for (int i = 0; i < kNbrPerLane; ++i) {
+        const int q = lane + kLanes * i;
+        const S* rf = B + (71 + 2 * q) * cp + j;
+        sf += arith<T>(rf[0]) * ng[i] + arith<T>(rf[cp]) * nf[i];
+        if (q < 13) {
+          const S* rc = B + (2 + 2 * q) * cp + j;
+          sc += arith<T>(rc[0]) * nc[i] + arith<T>(rc[cp]) * nf[i];
+          sg += arith<T>(B[(29 + q) * cp + j]) * ng[i];
+        } else {
+          const int d = q - 13;
+          sg += arith<T>(B[(42 + d + (d >= 13 ? 1 : 0)) * cp + j]) * ng[i];
+          if (d == 13) sg += arith<T>(B[55 * cp + j]) * nc[i];
+        }
+      }
+      sc = lane_sum(sc);
+      sg = lane_sum(sg);
+      sf = lane_sum(sf);
+      // the diagonal rows 0, 28, 70 hold the reciprocals of the pivots; the C
+      // row's own-f slot (U row 1) is applied after the f row is solved
       if (act && lane == 0) {
-        const T zf = (v2 - bF) * arith<T>(B[70 * c.cp + j]);
-        const T zg = (v1 - bG) * arith<T>(B[28 * c.cp + j]);
-        const T zc = (v0 - bC - arith<T>(B[1 * c.cp + j]) * zf) * arith<T>(B[0 * c.cp + j]);
-        vp[0] = zc;
-        vp[1] = zg;
-        vp[2] = zf;
+        const T zf = (v2 - sf) * arith<T>(B[70 * cp + j]);
+        const T zg = (v1 - sg) * arith<T>(B[28 * cp + j]);
+        const T zc = (v0 - sc - arith<T>(B[1 * cp + j]) * zf) * arith<T>(B[0 * cp + j]);
+        st3(vp, zc, zg, zf);
       }
     }
     __syncthreads();
@@ -497,9 +508,11 @@ __global__ void __launch_bounds__(ChunkCfg<S, kL>::CH * kL, 2) ras_solve(
   // scatter the owned part: (R^0)^T (otab: the owned points' global indices and offsets)
   for (int q = threadIdx.x; q < bx.nown; q += blockDim.x) {
     const int2 e = otab[bx.ooff + q];
-    z[e.x] = (double)v[e.y];
-    z[e.x + 1] = (double)v[e.y + 1];
-    z[e.x + 2] = (double)v[e.y + 2];
+    T a0, a1, a2;
+    ld3(v + e.y, a0, a1, a2);
+    z[e.x] = (double)a0;
+    z[e.x + 1] = (double)a1;
+    z[e.x + 2] = (double)a2;
   }
 }
 
@@ -538,59 +551,52 @@ struct SolveShape {
   int ch, cpmax, nstage, lanes;
   bool smem_vec;
 };
-template <typename T, bool SMEM, int L>
+template <typename T, bool SMEM>
 const void* solve_kernel() {
-  return (const void*)ras_solve<T, SMEM, L>;
+  return (const void*)ras_solve<T, SMEM>;
 }
 // A requested shape (ras_setup_shape): 0 in a field leaves it to the chooser.
 struct ShapeRequest {
   int ch = 0, nstage = 0, lanes = 0, place = 0;   // place: 1 shared-memory vector, 2 global-memory vector
 };
-template <typename T, int L>
-kkt_status shape_candidates(int nbox, long long max_pad, int nsm, const ShapeRequest& req, SolveShape* best,
-                            long long* best_key) {
-  if (req.lanes != 0 && req.lanes != L) return KKT_OK;
-  const int cands[3] = {ChunkCfg<T, L>::CH, ChunkCfg<T, L>::CH2, ChunkCfg<T, L>::CH3};
-  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// Picks the best shape allowed by `req`; KKT_ERR_ARG when none is.
+template <typename T>
+kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, const ShapeRequest& req, SolveShape* out) {
+  if (req.lanes != 0 && req.lanes != kLanes) {
+    set_error("ras_setup: the subdomain solve runs 4 lanes per point");
+    return KKT_ERR_ARG;
+  }
+  const int cands[3] = {ChunkCfg<T>::CH, ChunkCfg<T>::CH2, ChunkCfg<T>::CH3};
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kSmemLimit));
-  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kSmemLimit));
+  SolveShape best{};
+  long long best_key = -1;
   for (int ci = 0; ci < 3; ++ci)
     for (int ns = 2; ns <= kMaxStages; ++ns)
       for (int sv = 1; sv >= 0; --sv) {
-        const int ch = cands[ci], cp = chunk_stride<T, L>(ch);
+        const int ch = cands[ci], cp = chunk_stride<T>(ch);
         if ((req.ch && req.ch != ch) || (req.nstage && req.nstage != ns) || (req.place == 1 && !sv) ||
             (req.place == 2 && sv))
           continue;
         const size_t sm = solve_smem(cp, ns, sizeof(T), sizeof(typename SolveArith<T>::type), max_pad, sv != 0);
         if (sm > kSmemLimit) continue;
-        const int threads = (ch * L + 31) / 32 * 32;
+        const int threads = (ch * kLanes + 31) / 32 * 32;
         int per_sm = 0;
         KKT_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, sv ? solve_kernel<T, true, L>() : solve_kernel<T, false, L>(), threads, sm));
+            &per_sm, sv ? solve_kernel<T, true>() : solve_kernel<T, false>(), threads, sm));
         if (per_sm < 1) continue;
         const long long waves = (nbox + (long long)nsm * per_sm - 1) / ((long long)nsm * per_sm);
-        // smaller key is better; with the vector in shared memory 8 lanes per
-        // point, with the vector in global memory 4 (measured, see above)
-        const int lane_pref = sv ? (L == 8 ? 0 : 1) : (L == 4 ? 0 : 1);
-        const long long key =
-            (sv ? 0 : 1000000000LL) + waves * 100000 + (ns - 2) * 1000 + lane_pref * 100 + (100 - ch);
-        if (*best_key < 0 || key < *best_key) {
-          *best_key = key;
-          *best = SolveShape{ch, cp, ns, L, sv != 0};
+        // smaller key is better
+        const long long key = (sv ? 0 : 1000000000LL) + waves * 100000 + (ns - 2) * 1000 + (100 - ch);
+        if (best_key < 0 || key < best_key) {
+          best_key = key;
+          best = SolveShape{ch, cp, ns, kLanes, sv != 0};
         }
       }
-  return KKT_OK;
-}
-// Picks the best shape allowed by `req`; KKT_ERR_ARG when none is.
-template <typename T>
-kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, const ShapeRequest& req, SolveShape* out) {
-  SolveShape best{};
-  long long best_key = -1;
-  KKT_TRY((shape_candidates<T, 4>(nbox, max_pad, nsm, req, &best, &best_key)));
-  if constexpr (LaneSet<T>::N > 1) KKT_TRY((shape_candidates<T, 8>(nbox, max_pad, nsm, req, &best, &best_key)));
   if (best_key < 0) {
-    set_error("ras_setup: no subdomain-solve shape fits the request (chunk size, ring depth, lanes and vector "
+    set_error("ras_setup: no subdomain-solve shape fits the request (chunk size, ring depth and vector "
               "placement must be a compiled combination that fits in shared memory)");
     return KKT_ERR_ARG;
   }
@@ -643,19 +649,18 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
     set_error("ras_setup: internal slot table mismatch");
     return KKT_ERR_ARG;
   }
-  KKT_TRY(upload_slot_tables(T));
 
   ras_precond* m = new (std::nothrow) ras_precond();
   if (!m) return KKT_ERR_NOMEM;
   m->prob = p;
   m->prec = factor_prec;
   m->local = local;
-  auto stride = [&](int n) { return chunk_stride_of(factor_prec, m->lanes, n); };
+  auto stride = [&](int n) { return chunk_stride_of(factor_prec, n); };
   std::vector<std::pair<int, int>> pr[4];
   for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
   {
     // largest padded local vector: boxes are products of one part per axis
-    long long pad = 3;
+    long long pad = kVecWidth;
     for (int a = 0; a < 4; ++a) {
       int mx = 0;
       for (const auto& q : pr[a])
@@ -725,7 +730,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           b.voff = voff;
           b.poff = (long long)perm.size();
           b.loff = (long long)lptr.size();
-          voff += 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2);
+          voff += (long long)kVecWidth * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2);
           // counting sort of the points by wavefront
           std::vector<int> cnt(b.nlev + 1, 0);
           for (int kt = 0; kt < b.lt; ++kt)
@@ -752,7 +757,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
           {
             const long long sy = b.lx + 2, sz = sy * (b.ly + 2), st = sz * (b.lz + 2);
             auto pad = [&](int kx, int ky, int kz, int kt) {
-              return (int)(3 * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1)));
+              return (int)(kVecWidth * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1)));
             };
             auto glob = [&](int kx, int ky, int kz, int kt) {
               return (int)(3 * ((long long)(b.t0 + kt) * p->N + (b.x0 + kx) +
@@ -828,7 +833,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   m->vcount = voff;
   m->max_pad = 0;
   for (const BoxDesc& b : boxes)
-    m->max_pad = std::max(m->max_pad, 3LL * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2));
+    m->max_pad = std::max(m->max_pad, (long long)kVecWidth * (b.lx + 2) * (b.ly + 2) * (b.lz + 2) * (b.lt + 2));
   // bytes of a stored factor value and of a local-vector value
   const size_t esz = factor_prec == 64 ? sizeof(double) : (factor_prec == 32 ? sizeof(float) : 2);
   const size_t vsz = factor_prec == 64 ? sizeof(double) : sizeof(float);
@@ -906,32 +911,23 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
 
 namespace {
 
-template <typename S, int L>
-kkt_status launch_solve_l(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
-                          cudaStream_t s) {
+template <typename S>
+kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
+                        cudaStream_t s, const int* gate = nullptr) {
   using T = typename SolveArith<S>::type;
-  const int threads = (m->ch * L + 31) / 32 * 32;
+  const int threads = (m->ch * kLanes + 31) / 32 * 32;
   const int bstride = kLRanks * m->cpmax;
+  // (the dynamic shared-memory limit of both instances is raised at set-up, in choose_solve_shape)
   const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(S), sizeof(T), m->max_pad, m->smem_vec);
-  if (m->smem_vec) {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, true, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<S, true, L><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
-                                                         m->gtab, m->otab, m->vtab, bstride, m->nstage, m->status);
-  } else {
-    KKT_TRY_CUDA(cudaFuncSetAttribute(ras_solve<S, false, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ras_solve<S, false, L><<<m->nbox, threads, smem, s>>>(m->boxes, m->perm, m->chunks, (const S*)m->F, V, r, z,
-                                                          m->gtab, m->otab, m->vtab, bstride, m->nstage, m->status);
-  }
+  if (m->smem_vec)
+    ras_solve<S, true><<<m->nbox, threads, smem, s>>>(m->boxes, m->chunks, (const S*)m->F, V, r, z, m->gtab,
+                                                      m->otab, m->vtab, bstride, m->nstage, m->status, gate);
+  else
+    ras_solve<S, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->chunks, (const S*)m->F, V, r, z, m->gtab,
+                                                       m->otab, m->vtab, bstride, m->nstage, m->status, gate);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
-}
-template <typename S>
-kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
-                        cudaStream_t s) {
-  if constexpr (LaneSet<S>::N > 1)
-    if (m->lanes == 8) return launch_solve_l<S, 8>(m, r, z, V, s);
-  return launch_solve_l<S, 4>(m, r, z, V, s);
 }
 
 }  // namespace
@@ -961,12 +957,12 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   return ras_factor_status(m);
 }
 
-kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s) {
+kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate) {
   TimedScope timed(&m->timing, s);
-  if (m->local == 1) return ras_lu_solve(m, r, z, s);
-  if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s);
-  if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s);
-  return launch_solve<__nv_bfloat16>(m, r, z, (float*)m->V, s);
+  if (m->local == 1) return ras_lu_solve(m, r, z, s, gate);
+  if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s, gate);
+  if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s, gate);
+  return launch_solve<__nv_bfloat16>(m, r, z, (float*)m->V, s, gate);
 }
 
 kkt_status ras_check(ras_precond* m) {
@@ -991,8 +987,8 @@ extern "C" kkt_status ras_setup_shape(kkt_problem* p, const int nsub[4], int ove
     return KKT_ERR_ARG;
   }
   if (shape[0] < 0 || shape[1] < 0 || (shape[1] != 0 && (shape[1] < 2 || shape[1] > kMaxStages)) ||
-      (shape[2] != 0 && shape[2] != 4 && shape[2] != 8) || shape[3] < 0 || shape[3] > 2) {
-    set_error("ras_setup_shape: shape = {chunk points >= 0, ring buffers 0 or 2..4, lanes 0, 4 or 8, "
+      (shape[2] != 0 && shape[2] != kLanes) || shape[3] < 0 || shape[3] > 2) {
+    set_error("ras_setup_shape: shape = {chunk points >= 0, ring buffers 0 or 2..4, lanes 0 or 4, "
               "vector placement 0, 1 or 2}");
     return KKT_ERR_ARG;
   }

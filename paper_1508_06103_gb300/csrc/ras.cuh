@@ -43,6 +43,7 @@ constexpr int kMaxLuBand = 2048;
 constexpr int kMaxLuUnknowns = 28672;
 
 struct ras_precond {
+  unsigned long long uid = next_handle_uid();
   kkt_problem* prob = nullptr;
   int prec = 64;               // factor storage: 64, 32, or 16 (BF16; factorisation and solve in FP32)
   int nbox = 0;
@@ -93,6 +94,7 @@ kkt_status ras_factor_launch64(ras_precond* m, cudaStream_t s);
 kkt_status ras_factor_launch16(ras_precond* m, cudaStream_t s);   // FP32 factorisation, BF16 store
 // exact banded LU (lu.cu)
 kkt_status ras_lu_factor(ras_precond* m, cudaStream_t s);
-kkt_status ras_lu_solve(ras_precond* m, const double* r, double* z, cudaStream_t s);
-kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s);
+kkt_status ras_lu_solve(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate);
+// the subdomain solve z = M^{-1} r on s; its kernel returns at once while *gate reads 0
+kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate = nullptr);
 kkt_status ras_check(ras_precond* m);

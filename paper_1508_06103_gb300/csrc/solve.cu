@@ -21,6 +21,7 @@
 #include "ras.cuh"
 
 struct coarse_level {
+  unsigned long long uid = next_handle_uid();
   kkt_problem* fine = nullptr;
   kkt_problem* cp = nullptr;         // coarse problem (owned)
   ras_precond* cras = nullptr;       // coarse one-level RAS (owned)
@@ -32,7 +33,6 @@ struct coarse_level {
   float *cx32 = nullptr, *cy32 = nullptr;   // coarse FP32 scratch
   float *fx32 = nullptr, *fy32 = nullptr;   // fine FP32 scratch
   GmresWork ws;
-  int last_coarse_iters = 0;
   cudaStream_t aux = nullptr;        // two_level_refactor: stream of the coarse factorisation
   cudaEvent_t fork = nullptr, join = nullptr;
 };
@@ -50,7 +50,8 @@ struct Grid4 {
 // (vectors stay FP64 in memory).
 template <typename A>
 __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ yc,
-                              double* __restrict__ y) {
+                              double* __restrict__ y, const int* gate) {
+  if (gated_off(gate)) return;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)f.N * f.L) return;
   const int n = (int)(idx / f.N);
@@ -90,7 +91,8 @@ __global__ void interp_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, 
 // interp_kernel.
 template <typename A>
 __global__ void restrict_kernel(Grid4 f, Grid4 c, int rx, int ry, int rz, int rt, const double* __restrict__ x,
-                                double* __restrict__ rc) {
+                                double* __restrict__ rc, const int* gate) {
+  if (gated_off(gate)) return;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)c.N * c.L) return;
   const int n = (int)(idx / c.N);
@@ -130,10 +132,13 @@ Grid4 grid_of(const kkt_problem* p) { return Grid4{p->nx, p->ny, p->nz, p->L, p-
 struct KktOp : Operator {
   kkt_problem* p;
   explicit KktOp(kkt_problem* p_) : p(p_) {}
-  kkt_status apply(const double* x, double* y, cudaStream_t s) override {
+  kkt_status apply(const double* x, double* y, cudaStream_t s, const int* gate) override {
     TimedScope t(&p->mv_timing, s);
-    return launch_matvec64(p->dev(), x, y, s);
+    DevProblem d = p->dev();
+    d.gate = gate;
+    return launch_matvec64(d, x, y, s);
   }
+  unsigned long long uid() const override { return p->uid * 4 + (unsigned long long)p->reg; }
 };
 
 // The coarse operator inside the preconditioner: FP64, or FP32 arithmetic on
@@ -143,41 +148,55 @@ struct CoarseOp : Operator {
   int prec;
   float *x32, *y32;
   CoarseOp(kkt_problem* p_, int prec_, float* a, float* b) : p(p_), prec(prec_), x32(a), y32(b) {}
-  kkt_status apply(const double* x, double* y, cudaStream_t s) override {
-    if (prec == 64) return launch_matvec64(p->dev(), x, y, s);
-    return launch_matvec32_d(p->dev(), x, y, x32, y32, s);
+  kkt_status apply(const double* x, double* y, cudaStream_t s, const int* gate) override {
+    DevProblem d = p->dev();
+    d.gate = gate;
+    if (prec == 64) return launch_matvec64(d, x, y, s);
+    return launch_matvec32_d(d, x, y, x32, y32, s);
   }
+  unsigned long long uid() const override { return p->uid * 4 + (unsigned long long)p->reg; }
 };
 
 struct RasOp : Operator {
   ras_precond* m;
   explicit RasOp(ras_precond* m_) : m(m_) {}
-  kkt_status apply(const double* x, double* y, cudaStream_t s) override { return ras_launch(m, x, y, s); }
+  kkt_status apply(const double* x, double* y, cudaStream_t s, const int* gate) override {
+    return ras_launch(m, x, y, s, gate);
+  }
+  unsigned long long uid() const override { return m->uid; }
 };
 
-kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double* z, cudaStream_t s) {
+// The multiplicative two-level hybrid; every kernel returns at once while
+// *gate reads 0 (the coarse GMRES is gated by its own state, which starts
+// only when *gate is live).
+kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double* z, cudaStream_t s,
+                     const int* gate) {
   kkt_problem* pf = c->fine;
   kkt_problem* pc = c->cp;
   const Grid4 gf = grid_of(pf), gc = grid_of(pc);
   const unsigned rblocks = (unsigned)((pc->P + 255) / 256), iblocks = (unsigned)((pf->P + 255) / 256);
-  if (c->prec == 64) restrict_kernel<double><<<rblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
-  else restrict_kernel<float><<<rblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc);
+  if (c->prec == 64)
+    restrict_kernel<double><<<rblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc, gate);
+  else
+    restrict_kernel<float><<<rblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, x, c->rc, gate);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   CoarseOp Ac(pc, c->prec, c->cx32, c->cy32);
   RasOp Mc(c->cras);
   GmresResult r;
-  KKT_TRY(gmres_run(Ac, &Mc, c->rc, c->yc, c->ws, c->c_maxit, c->c_rtol, c->c_maxit, false, true, &r, s));
-  if (r.status < 0) return r.status;
-  c->last_coarse_iters = r.iters;
-  if (c->prec == 64) interp_kernel<double><<<iblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
-  else interp_kernel<float><<<iblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y);
+  KKT_TRY(gmres_run(Ac, &Mc, c->rc, c->yc, c->ws, c->c_maxit, c->c_rtol, c->c_maxit, false, true, &r, s, gate));
+  if (c->prec == 64)
+    interp_kernel<double><<<iblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y, gate);
+  else
+    interp_kernel<float><<<iblocks, 256, 0, s>>>(gf, gc, c->rx, c->ry, c->rz, c->rt, c->yc, c->y, gate);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
-  if (c->prec == 64) KKT_TRY(launch_residual(pf->dev(), x, c->y, c->t, s));   // t = x - F_h y
-  else KKT_TRY(launch_residual32(pf->dev(), x, c->y, c->t, c->fx32, c->fy32, s));
-  KKT_TRY(ras_launch(fine, c->t, z, s));
-  KKT_TRY(vec_axpby(z, 1.0, c->y, 1.0, pf->n, s));          // z = M^{-1} t + y
+  DevProblem df = pf->dev();
+  df.gate = gate;
+  if (c->prec == 64) KKT_TRY(launch_residual(df, x, c->y, c->t, s));   // t = x - F_h y
+  else KKT_TRY(launch_residual32(df, x, c->y, c->t, c->fx32, c->fy32, s));
+  KKT_TRY(ras_launch(fine, c->t, z, s, gate));
+  KKT_TRY(vec_axpby(z, 1.0, c->y, 1.0, pf->n, s, gate));   // z = M^{-1} t + y
   return KKT_OK;
 }
 
@@ -185,7 +204,10 @@ struct TwoLevelOp : Operator {
   coarse_level* c;
   ras_precond* fine;
   TwoLevelOp(coarse_level* c_, ras_precond* f_) : c(c_), fine(f_) {}
-  kkt_status apply(const double* x, double* y, cudaStream_t s) override { return two_level(c, fine, x, y, s); }
+  kkt_status apply(const double* x, double* y, cudaStream_t s, const int* gate) override {
+    return two_level(c, fine, x, y, s, gate);
+  }
+  unsigned long long uid() const override { return (c->uid << 32) ^ fine->uid; }
 };
 
 }  // namespace
@@ -275,7 +297,7 @@ extern "C" kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const 
     set_error("two_level_apply: the fine preconditioner belongs to another problem");
     return KKT_ERR_ARG;
   }
-  return two_level(c, fine, x, z, (cudaStream_t)stream);
+  return two_level(c, fine, x, z, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" kkt_status coarse_refactor(coarse_level* c, void* stream) {
@@ -355,7 +377,7 @@ extern "C" kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* 
   TwoLevelOp T(c, m);
   Operator* M = c ? (Operator*)&T : (m ? (Operator*)&R : nullptr);
   GmresResult res;
-  KKT_TRY(gmres_run(A, M, b, x, ws, restart, rtol, maxit, true, false, &res, s));
+  KKT_TRY(gmres_run(A, M, b, x, ws, restart, rtol, maxit, true, false, &res, s, nullptr, true));
   if (m) KKT_TRY(ras_check(m));
   if (c) KKT_TRY(ras_check(c->cras));
   if (iters) *iters = res.iters;

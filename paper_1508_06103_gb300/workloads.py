@@ -71,6 +71,7 @@ class Workload:
     coarse_cells: Tuple[int, int, int] | None = None
     coarse_M: int | None = None
     coarse_overlap: int = 1
+    coarse_nsub: Tuple[int, int, int, int] | None = None   # split of the coarse level (None: as nsub)
     coarse_rtol: float = 1e-1
     coarse_maxit: int = 4
     restart: int = 30
@@ -95,6 +96,11 @@ class Workload:
     @property
     def unknowns(self) -> int:
         return 3 * self.P
+
+    @property
+    def coarse_split(self) -> Tuple[int, int, int, int]:
+        """Subdomains of the coarse level's one-level RAS."""
+        return self.coarse_nsub if self.coarse_nsub is not None else self.nsub
 
     @property
     def tau(self) -> float:
@@ -264,7 +270,7 @@ def large() -> Workload:
         dirichlet_faces=FACE_X0, a_cell=a, v_cell=v, sensor_xyz=sensor_lattice(8, L),
         beta1=beta / 100, beta2=beta, sources=srcs, noise_eps=0.02, noise_seed=5,
         nsub=(8, 8, 8, 8), overlap=2, local="ilu0", coarse_cells=(16, 16, 16), coarse_M=32,
-        coarse_overlap=1, restart=40, rtol=1e-8,
+        coarse_overlap=1, coarse_nsub=(4, 4, 4, 4), restart=40, rtol=1e-8,
     )
 
 

@@ -11,6 +11,7 @@ outside its CPU-baseline leg.
 
     python tests/golden/make_observations.py              # observations_mid_32x32x32x64.txt
     python tests/golden/make_observations.py --refine 2   # ..._refined2.txt (not used by default)
+    python tests/golden/make_observations.py --workload large   # observations_large_64x64x64x128.txt
 """
 
 import os
@@ -25,10 +26,10 @@ from oracle import forward, kkt  # noqa: E402
 from paper_1508_06103_gb300 import workloads as W  # noqa: E402
 
 
-def write(w, path, refine=1):
+def write(w, path, refine=1, solver="lu"):
     if refine == 1:
         p = kkt.Problem.from_workload(w)
-        C = forward.forward_march(p, w.true_source())
+        C = forward.forward_march(p, w.true_source(), solver=solver)
         obs = forward.observations(p, C, w.noise(), w.noise_eps)
     else:
         wf = W.refined(w, refine)
@@ -46,7 +47,10 @@ if __name__ == "__main__":
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--workload", choices=["mid", "large"], default="mid")
     a = ap.parse_args()
-    w = W.mid()
+    w = W.mid() if a.workload == "mid" else W.large()
     suffix = "" if a.refine == 1 else f"_refined{a.refine}"
-    write(w, os.path.join(HERE, f"observations_{w.name}{suffix}.txt"), a.refine)
+    # the 65^3-node step matrix is too large for sparse LU: iterative steps to 1e-13
+    write(w, os.path.join(HERE, f"observations_{w.name}{suffix}.txt"), a.refine,
+          "lu" if a.workload == "mid" else "bicgstab")

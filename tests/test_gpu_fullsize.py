@@ -1,22 +1,33 @@
-"""Full-size GPU solves checked by properties the oracle evaluates at any size.
+"""Full-size GPU solves checked against the oracle.
 
 * 32^3 cells x 64 steps (7,007,715 unknowns), two-level RAS, FGMRES(30):
-  the oracle's level-wise F_h gives the true relative residual of the GPU
-  solution, which must be <= 1e-8 (the stop test) in the FP64 form and the
-  mixed form with FP32 or BF16-stored factors; the recovered sources of the
-  mixed forms, solved to 1e-10, agree with the FP64 form's to 1e-5 relative
-  L2 (the accuracy bound stated for the mixed form).
+  - the oracle's level-wise F_h gives the true relative residual of the GPU
+    solution, which must be <= 1e-8 (the stop test), in the FP64 form and the
+    mixed forms with FP32 or BF16-stored factors;
+  - the solution itself against the oracle's reduced-space solution of the same
+    system (tests/golden/reduced_solution_mid_32x32x32x64.txt, written by
+    tests/golden/make_reduced_solution.py from oracle/ alone: the paper's
+    traditional method, time marches and GMRES on f to 1e-13, true KKT
+    residual 2.5e-15): the FP64 form solved to 1e-13 matches U to 1e-8
+    relative (2-norm over 4096 seeded samples, and the norm of U), the mixed
+    forms solved to 1e-10 match the recovered source f to 1e-5 relative
+    (4096 seeded samples of f, and its norm).  The KKT system is
+    ill-conditioned, so the comparisons follow solves tighter than the 1e-8
+    stop test.
 * The benchmark's fine subdomain solve itself (local vectors in global
-  memory, 4 lanes per point), FP64 and FP32 factors, at 32^3 x 64: z on the
-  owned points of two of its 256 boxes against the oracle's ILU(0) of those
-  boxes (RAS is a disjoint union over the owned sets, so those entries depend
-  on that box alone), with the small-case bars.
+  memory), FP64 and FP32 factors, at 32^3 x 64: z on the owned points of two
+  of its 256 boxes against the oracle's ILU(0) of those boxes (RAS is a
+  disjoint union over the owned sets, so those entries depend on that box
+  alone), with the small-case bars.
 * 8^3 cells x 16 implicit-Euler steps (37,179 unknowns), one-level RAS
-  2x2x2x2, overlap 1, exact local LU (and ILU(0)): the GPU solution agrees
-  with the oracle's solution of the same system to 1e-8 relative after both
-  are solved to 1e-13.
+  2x2x2x2, overlap 1, exact local LU and ILU(0): the GPU solution after a
+  1e-13 solve agrees to 1e-8 with the sparse direct solution of F_h
+  (tests/golden/direct_solution_tiny_8x8x8x16.txt, tests/golden/make_direct_solution.py),
+  and the exact-LU form needs no more iterations than the oracle's own GMRES
+  with the same preconditioner.
 """
 
+import importlib.util
 import os
 
 import numpy as np
@@ -32,6 +43,16 @@ from paper_1508_06103_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 OBS = os.path.join(ROOT, "tests", "golden", "observations_mid_32x32x32x64.txt")
+REDUCED = os.path.join(ROOT, "tests", "golden", "reduced_solution_mid_32x32x32x64.txt")
+DIRECT = os.path.join(ROOT, "tests", "golden", "direct_solution_tiny_8x8x8x16.txt")
+
+
+def _golden(name):
+    """The reader of a golden-writing script under tests/golden (its read function)."""
+    spec = importlib.util.spec_from_file_location(name, os.path.join(ROOT, "tests", "golden", name + ".py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.read
 
 
 @pytest.fixture(scope="module")
@@ -112,23 +133,33 @@ def test_two_level_solve_full_size_true_residual(api, mid_setup, prec):
     assert its <= 40
 
 
-def test_mixed_and_fp64_sources_agree_full_size(api, mid_setup):
+def test_fp64_solution_matches_the_reduced_space_oracle(api, mid_setup):
     w, p, cobs, b, prob = mid_setup
-    _, f64, st64, _, _, _ = _solve(api, w, prob, cobs, 64, 1e-10)
-    _, f32, st32, _, _, _ = _solve(api, w, prob, cobs, 32, 1e-10)
-    _, f16, st16, _, _, _ = _solve(api, w, prob, cobs, 16, 1e-10)
-    assert st64 == 0 and st32 == 0 and st16 == 0
-    assert np.linalg.norm(f32 - f64) <= 1e-5 * np.linalg.norm(f64)
-    assert np.linalg.norm(f16 - f64) <= 1e-5 * np.linalg.norm(f64)
+    norms, iu, uref, _, _ = _golden("make_reduced_solution")(REDUCED)
+    x, f, st, its, rel, bd = _solve(api, w, prob, cobs, 64, 1e-13)
+    assert st == 0 and rel <= 1e-13
+    assert np.linalg.norm(x[iu] - uref) <= 1e-8 * np.linalg.norm(uref)
+    assert abs(np.linalg.norm(x) - norms["U"]) <= 1e-8 * norms["U"]
 
 
-def test_tiny_implicit_euler_one_level_matches_oracle(api):
+@pytest.mark.parametrize("prec", [32, 16])
+def test_mixed_form_source_matches_the_reduced_space_oracle(api, mid_setup, prec):
+    w, p, cobs, b, prob = mid_setup
+    norms, _, _, jf, fref = _golden("make_reduced_solution")(REDUCED)
+    x, f, st, its, rel, bd = _solve(api, w, prob, cobs, prec, 1e-10)
+    assert st == 0 and rel <= 1e-10
+    assert np.linalg.norm(x[jf] - fref) <= 1e-5 * np.linalg.norm(fref)
+    assert abs(np.linalg.norm(f) - norms["f"]) <= 1e-5 * norms["f"]
+
+
+def test_tiny_implicit_euler_one_level_matches_direct_solution(api):
     w = W.tiny(theta=1.0)
     p = okkt.Problem.from_workload(w)
     F = okkt.assemble(p)
     C = ofwd.forward_march(p, w.true_source())
     cobs = ofwd.observations(p, C, w.noise(), w.noise_eps)
     b = okkt.rhs(p, cobs)
+    unorm, iu, uref = _golden("make_direct_solution")(DIRECT)
     ref = osch.RAS(p, F, w.nsub, w.overlap, "lu")
     sol = okry.gmres(lambda u: F @ u, b, ref.apply, restart=30, rtol=1e-13, maxit=400)
     assert sol.converged
@@ -141,6 +172,7 @@ def test_tiny_implicit_euler_one_level_matches_oracle(api):
         x, st, its, rel = api.gmres_solve(prob, bd, ras=ras, restart=30, rtol=1e-13, maxit=3000)
         assert st == 0
         xe = x.cpu().numpy()
-        assert np.linalg.norm(xe - sol.x) <= 1e-8 * np.linalg.norm(sol.x)
+        assert np.linalg.norm(xe[iu] - uref) <= 1e-8 * np.linalg.norm(uref)
+        assert abs(np.linalg.norm(xe) - unorm) <= 1e-8 * unorm
         if local == "lu":
             assert its <= sol.iterations + 2  # the same preconditioner as the oracle's
