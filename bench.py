@@ -30,6 +30,7 @@ output line).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -480,6 +481,14 @@ def kernel_arm(args):
     y = torch.empty_like(x)
     out = {"kernel": args.kernel, "cells": c, "levels": M, "unknowns": prob.n}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.kernel == "peaks":
+        res = {}
+        for prec in (64, 32):
+            tf = [api.fma_peak(prec)[0] for _ in range(5)]
+            res[f"fp{prec}_fma_tflops"] = max(tf)
+            res[f"fp{prec}_fma_tflops_runs"] = tf
+        print(json.dumps({"kernel": "peaks", **res}))
+        return
     if args.kernel == "ras":
         shape = None if not (args.chunk or args.stages) else (args.chunk, args.stages, 0, 0)
         ras = api.RAS(prob, w.nsub, w.overlap, args.prec, shape=shape)
@@ -591,6 +600,8 @@ def large_arm(args):
 
     build.build()
     w = W.large()
+    if args.coarse_levels:
+        w = dataclasses.replace(w, coarse_M=args.coarse_levels)
     cobs = torch.from_numpy(np.loadtxt(OBS_FILE_LARGE, ndmin=2)).cuda()
     prob = api.Problem.from_workload(w)
     b, x = prob.zeros(), prob.zeros()
@@ -618,7 +629,7 @@ def large_arm(args):
         co.refactor_with(ras)
         x.zero_()
         _, st, its, rel = api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=w.restart, rtol=w.rtol,
-                                          maxit=2000)
+                                          maxit=args.maxit)
         prob.recover_source(x, out=f)
         last.update(status=st, iterations=its, relres=rel)
 
@@ -640,7 +651,9 @@ def large_arm(args):
     out = {
         "metric": "KKT solve s to 1e-8 rel. residual at 64^3x128 (FP32 subdomain solves, FGMRES(40))",
         "value": ms / 1e3, "unit": "s", "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
-        "workload": f"{w.name}: {prob.n:,} unknowns, 8^4 subdomains overlap 2, coarse 16^3 x 32 (4^4, overlap 1)",
+        "maxit": args.maxit, "ms_per_iteration": ms / max(1, last.get("iterations") or 1),
+        "workload": f"{w.name}: {prob.n:,} unknowns, 8^4 subdomains overlap 2, coarse {w.coarse_cells[0]}^3 x "
+                    f"{w.coarse_M} (4^4, overlap 1)",
         "status": last.get("status"), "iterations": last.get("iterations"), "true_relres": last.get("relres"),
         "setup_s": setup_s, "box_points": info["points"], "factor_gb": info["factor_values"] * info["value_bytes"] / 1e9,
         "device_memory_used_gb": (total - free) / 1e9, "device_memory_total_gb": total / 1e9,
@@ -664,7 +677,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["ras", "matvec", "sweep"], default=None,
+    ap.add_argument("--kernel", choices=["ras", "matvec", "sweep", "peaks"], default=None,
                     help="time one kernel on a member of the workload family instead of the full solve; "
                          "sweep: overlap and one/two-level sweep of the mixed-form solve")
     ap.add_argument("--cells", type=int, default=32)
@@ -675,6 +688,10 @@ def main():
     ap.add_argument("--stages", type=int, default=0, help="--kernel ras: copy-ring buffers (0: the library's choice)")
     ap.add_argument("--data", choices=["same-mesh", "refined2"], default="same-mesh",
                     help="observations: same-mesh forward solve (default) or one on a 2x finer mesh")
+    ap.add_argument("--maxit", type=int, default=400,
+                    help="--workload large: FGMRES iteration limit of a step (the solve converges slowly)")
+    ap.add_argument("--coarse-levels", type=int, default=0,
+                    help="--workload large: time steps of the coarse level (0: the workload's)")
     ap.add_argument("--workload", choices=["mid", "large"], default="mid",
                     help="large: time the 64^3 x 128 single solve instead of the default benchmark")
     args = ap.parse_args()

@@ -327,6 +327,16 @@ kkt_status ras_timing_read(ras_precond* m, int kernel, double* total_ms, long lo
 kkt_status kkt_timing_reset(kkt_problem* p, ras_precond* m);
 
 /*
+ * kkt_fma_peak -- measured multiply-add rate of the current device in FP64
+ *   (precision 64) or FP32 (32), in TFLOP/s (2 flops per FMA), from one
+ *   launch of independent register-resident FMA chains on every SM, timed
+ *   with CUDA events on `stream` (synchronises it); *ms (may be NULL) gets
+ *   the launch time.  Instrumentation: the denominator of the FP64 KKT
+ *   matvec's pipe fraction; the paper has no counterpart.  Errors: ARG, CUDA.
+ */
+kkt_status kkt_fma_peak(int precision, double* tflops, double* ms, void* stream);
+
+/*
  * recover_source -- f of the point-block vector U as an (M+1) x N array
  *   (Sec. 3.2 ordering; the recovered source of the inverse problem).
  */

@@ -231,6 +231,13 @@ def launch_count() -> int:
     return int(_lib.load().kkt_launch_count())
 
 
+def fma_peak(precision: int = 64, stream=None):
+    """(TFLOP/s, ms) of the device's multiply-add rate in FP64 or FP32 (kkt_fma_peak)."""
+    tf, ms = C.c_double(), C.c_double()
+    check(_lib.load().kkt_fma_peak(int(precision), C.byref(tf), C.byref(ms), _stream(stream)), "kkt_fma_peak")
+    return tf.value, ms.value
+
+
 def timing_enable(on: bool) -> bool:
     return bool(_lib.load().kkt_timing_enable(int(on)))
 
