@@ -176,6 +176,35 @@ kkt_status ras_setup_shape(kkt_problem* p, const int nsub[4], int overlap, int l
                            const int shape[4], ras_precond** out);
 
 /*
+ * ras_setup_batch -- one-level RAS of several independent problems solved
+ *   together (a batching form of this library; the paper solves one problem):
+ *   every problem is split by nsub (overlap, ILU(0) local solves, factor_prec as
+ *   in ras_setup) and the boxes of all problems form one list, largest first,
+ *   so one factorisation launch and one subdomain-solve launch cover all of
+ *   them.  Vectors of such a preconditioner concatenate the problems' unknowns
+ *   in the order given (problem k starts after the 3*N*(M+1) unknowns of
+ *   problems 0..k-1).  shape: NULL or as in ras_setup_shape (e.g. from
+ *   ras_autotune).  The problems must outlive the handle.  Synchronous;
+ *   errors: ARG, NOMEM, CUDA, ZERO_PIVOT.
+ */
+kkt_status ras_setup_batch(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap,
+                           int factor_prec, const int shape[4], ras_precond** out);
+
+/*
+ * ras_autotune -- choose the subdomain solve's shape by measurement: every
+ *   compiled chunk size with 2 and 3 copy buffers is set up on these problems
+ *   (split as in ras_setup_batch, ILU(0), factor_prec) and timed over `reps`
+ *   applies with CUDA events; shape_out gets the fastest {chunk points, ring
+ *   buffers, 4, 0} and *best_ms (may be NULL) its time per apply.  With a
+ *   cache_path (may be NULL) an earlier result for the same problem sizes,
+ *   split, precision and device is read from that text file instead, and a
+ *   new one is appended.  Synchronous; a tuning aid with no counterpart in the
+ *   paper.  Errors: ARG, NOMEM, CUDA, ZERO_PIVOT.
+ */
+kkt_status ras_autotune(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap, int factor_prec,
+                        int reps, const char* cache_path, int shape_out[4], double* best_ms);
+
+/*
  * ras_info -- sizes of a preconditioner: boxes, points of all extended boxes
  *   (with overlap), stored factor values and bytes per value.  Any output may
  *   be NULL.
@@ -284,6 +313,24 @@ kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const double* x, 
 kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* c, const double* b, double* x,
                        int restart, double rtol, int maxit, int flexible, int* iters,
                        double* true_relres, void* stream);
+
+/*
+ * gmres_solve_batch -- flexible GMRES(restart) on several independent problems
+ *   at once, right-preconditioned by their ras_setup_batch preconditioner m
+ *   (probs in the same order): b, x device FP64 vectors over the concatenated
+ *   unknowns (x's initial contents are ignored: zero initial guess).  The
+ *   problems step in lockstep; every problem has its own Arnoldi process,
+ *   rotations and stop test on the device (stop at its own true residual
+ *   ||b_k - F_k x_k|| <= rtol ||b_k||), and a problem that has stopped no
+ *   longer does work.  A restart cycle of all problems is one captured CUDA
+ *   graph, replayed with one host round trip per cycle.  iters, true_relres,
+ *   status: host arrays of nprob entries (may be NULL).  Returns OK when every
+ *   problem converged, else the most severe problem status (errors first).
+ *   Synchronises the stream.
+ */
+kkt_status gmres_solve_batch(kkt_problem* const* probs, int nprob, ras_precond* m, const double* b, double* x,
+                             int restart, double rtol, int maxit, int* iters, double* true_relres, int* status,
+                             void* stream);
 
 /*
  * ras_refactor -- recompute the ILU(0) factors of an existing preconditioner in

@@ -53,6 +53,13 @@ SIGNATURES = {
     "ras_solve_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int)]),
     "ras_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p]),
+    "ras_setup_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_void_p)]),
+    "ras_autotune": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
+                               C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "gmres_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int), C.c_void_p]),
     "ras_selftest_wait": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "coarse_refactor": (C.c_int, [C.c_void_p, C.c_void_p]),
     "two_level_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

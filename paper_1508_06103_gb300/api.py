@@ -267,3 +267,57 @@ def gmres_solve(prob: Problem, b: torch.Tensor, x: Optional[torch.Tensor] = None
                          int(restart), float(rtol), int(maxit), int(flex), C.byref(it), C.byref(rel), _stream(stream))
     check(st, "gmres_solve")
     return x, st, it.value, rel.value
+
+
+def _handles(probs: Sequence[Problem]):
+    return (C.c_void_p * len(probs))(*[p.h.value for p in probs])
+
+
+class BatchRAS(RAS):
+    """One-level RAS of several independent problems in one set of launches (ras_setup_batch).
+
+    Vectors concatenate the problems' unknowns in the order of `probs`.
+    """
+
+    def __init__(self, probs: Sequence[Problem], nsub: Sequence[int], overlap: int, factor_prec: int = 32,
+                 shape: Optional[Sequence[int]] = None):
+        self._lib = _lib.load()
+        self.prob = probs[0]
+        self.probs = list(probs)
+        self.offsets = np.cumsum([0] + [p.n for p in probs]).tolist()
+        ns = (C.c_int * 4)(*[int(v) for v in nsub])
+        sh = None if shape is None else (C.c_int * 4)(*[int(v) for v in shape])
+        h = C.c_void_p()
+        check(self._lib.ras_setup_batch(_handles(probs), len(probs), ns, int(overlap), int(factor_prec), sh,
+                                        C.byref(h)), "ras_setup_batch")
+        self.h = h
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+
+def autotune(probs: Sequence[Problem], nsub: Sequence[int], overlap: int, factor_prec: int = 32, reps: int = 3,
+             cache_path: Optional[str] = None):
+    """(shape, ms per apply) of the fastest subdomain-solve shape on these problems (ras_autotune)."""
+    ns = (C.c_int * 4)(*[int(v) for v in nsub])
+    out = (C.c_int * 4)()
+    ms = C.c_double()
+    check(_lib.load().ras_autotune(_handles(probs), len(probs), ns, int(overlap), int(factor_prec), int(reps),
+                                   cache_path.encode() if cache_path else None, out, C.byref(ms)), "ras_autotune")
+    return tuple(out), ms.value
+
+
+def gmres_solve_batch(probs: Sequence[Problem], ras: BatchRAS, b: torch.Tensor, x: Optional[torch.Tensor] = None,
+                      restart: int = 30, rtol: float = 1e-8, maxit: int = 1000, stream=None):
+    """Solve every problem's F_k x_k = b_k together; returns (x, status, per-problem lists of
+    status, iterations and true relative residuals)."""
+    lib = _lib.load()
+    if x is None:
+        x = torch.zeros_like(b)
+    n = len(probs)
+    its, rel, sts = (C.c_int * n)(), (C.c_double * n)(), (C.c_int * n)()
+    st = lib.gmres_solve_batch(_handles(probs), n, ras.h, _ptr(b), _ptr(x), int(restart), float(rtol), int(maxit),
+                               its, rel, sts, _stream(stream))
+    check(st, "gmres_solve_batch")
+    return x, st, list(sts), list(its), list(rel)

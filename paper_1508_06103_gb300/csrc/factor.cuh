@@ -41,10 +41,12 @@ constexpr int factor_threads = sizeof(T) == 4 ? 192 : 128;
 // at n-1, n, n+1), plus the G row's two sensor slots at the centre.  Also
 // writes each box's unit row.
 template <typename T>
-__global__ void __launch_bounds__(kGatherThreads) gather_chunks(DevProblem p, const BoxDesc* __restrict__ boxes,
+__global__ void __launch_bounds__(kGatherThreads) gather_chunks(const DevProblem* __restrict__ probs,
+                                                                const BoxDesc* __restrict__ boxes,
                                                                 const int* __restrict__ perm,
                                                                 const int2* __restrict__ ptab, T* __restrict__ F) {
   const BoxDesc bx = boxes[blockIdx.y];
+  const DevProblem p = probs[bx.prob];
   T* Fb = F + bx.foff;
   if (blockIdx.x == 0)
     for (int s = threadIdx.x; s < kSlots; s += blockDim.x)
@@ -161,11 +163,10 @@ __global__ void __launch_bounds__(factor_threads<T>, 2) ilu0_factor(const BoxDes
 // gather, then factor, in place on F (chunk layout); both on stream s
 template <typename T>
 kkt_status factor_launch(ras_precond* m, T* F, cudaStream_t s) {
-  const DevProblem dp = m->prob->dev();
   long long pmax = 0;
   for (const BoxDesc& b : m->boxes_h) pmax = std::max(pmax, b.P);
   const dim3 g((unsigned)((pmax + kGatherThreads - 1) / kGatherThreads), m->nbox);
-  gather_chunks<T><<<g, kGatherThreads, 0, s>>>(dp, m->boxes, m->perm, m->ptab, F);
+  gather_chunks<T><<<g, kGatherThreads, 0, s>>>(m->dprobs, m->boxes, m->perm, m->ptab, F);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   {

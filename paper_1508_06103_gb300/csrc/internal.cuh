@@ -224,6 +224,28 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
                      double rtol, int maxit, bool check_true, bool zero_guess, GmresResult* res,
                      cudaStream_t s, const int* parent = nullptr, bool graph = false);
 
+// Workspace of gmres_run_batch: one FGMRES workspace over the concatenated
+// unknowns of all problems, one state and set of small arrays per problem.
+struct BatchWork {
+  GmresWork ws;
+  std::vector<long long> off;   // nprob + 1 offsets of the problems' unknowns
+  GmresState* st = nullptr;     // device, one per problem
+  GmresState* st_host = nullptr;
+  double* small = nullptr;      // device, GmresWork::doubles(m) per problem
+  kkt_status alloc(const std::vector<long long>& off_, int m_);
+  void release();
+  ~BatchWork() { release(); }
+};
+
+// Flexible GMRES on several independent problems in lockstep (one captured
+// cycle for all when `graph`); A[k] is problem k's operator on its part of the
+// concatenated vectors, M the preconditioner of all problems, whose kernels
+// read the gate of problem k at stride sizeof(GmresState) ints; res[k] gets
+// problem k's iterations, true relative residual and status.
+kkt_status gmres_run_batch(std::vector<Operator*>& A, Operator& M, const double* b, double* x, BatchWork& bw,
+                           int restart, double rtol, int maxit, std::vector<GmresResult>& res, cudaStream_t s,
+                           bool graph);
+
 kkt_status vec_copy(double* y, const double* x, long long n, cudaStream_t s, const int* gate = nullptr);
 kkt_status vec_zero(double* y, long long n, cudaStream_t s);
 kkt_status vec_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s,

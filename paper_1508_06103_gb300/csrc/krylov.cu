@@ -144,7 +144,7 @@ __global__ void gm_begin(GmresState* st, double* g, int m, const int* parent) {
   st->k = 0;
   st->ran = 0;
   st->steps = 0;
-  if ((parent != nullptr && *parent == 0) || st->flag == kGmNonFinite) {
+  if ((parent != nullptr && *parent == 0) || st->flag == kGmNonFinite || st->flag == kGmBreakdown) {
     st->active = 0;
     return;
   }
@@ -337,18 +337,20 @@ kkt_status after_replay(CycleGraph& gr, int steps) {
   return KKT_OK;
 }
 
-// Capture one restart cycle into gr (on the work's own stream, which forks
-// from and joins into nothing: the graph is launched on the caller's stream).
-kkt_status capture_cycle(Operator& A, Operator* M, const double* b, double* x, GmresWork& ws, int m,
-                         const unsigned long long* key) {
+// Capture one restart cycle, enqueued by `enqueue` on the given stream, into
+// gr (on the work's own stream, which forks from and joins into nothing: the
+// graph is launched on the caller's stream).
+template <typename Enqueue>
+kkt_status capture_cycle(GmresWork& ws, int m, const unsigned long long* key, int timed_per_step,
+                         Enqueue&& enqueue) {
   CycleGraph& gr = ws.graph;
   gr.release();
   if (!ws.cap) KKT_TRY_CUDA(cudaStreamCreateWithFlags(&ws.cap, cudaStreamNonBlocking));
   CaptureTiming& ct = gr.timing;
   ct.clear();
   if (g_timing_on.load()) {
-    // launches timed per step: outer matvec, fine and coarse subdomain solves
-    const size_t npairs = 8 * (size_t)m + 16;
+    // launches timed per step: outer matvecs, fine and coarse subdomain solves
+    const size_t npairs = (size_t)timed_per_step * m + 16;
     for (size_t i = 0; i < npairs; ++i) {
       cudaEvent_t e0, e1;
       KKT_TRY_CUDA(cudaEventCreate(&e0));
@@ -359,7 +361,7 @@ kkt_status capture_cycle(Operator& A, Operator* M, const double* b, double* x, G
   const long long before = g_kernel_launches.load();
   KKT_TRY_CUDA(cudaStreamBeginCapture(ws.cap, cudaStreamCaptureModeThreadLocal));
   g_capture = &ct;
-  const kkt_status st = enqueue_cycle(A, M, b, x, ws, m, true, nullptr, ws.cap);
+  const kkt_status st = enqueue(ws.cap);
   g_capture = nullptr;
   cudaGraph_t graph = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(ws.cap, &graph);
@@ -532,7 +534,9 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
   for (;;) {
     if (graph) {
       if (!ws.graph.exec || std::memcmp(ws.graph.key, key, sizeof(key)) != 0)
-        KKT_TRY(capture_cycle(A, M, b, x, ws, m, key));
+        KKT_TRY(capture_cycle(ws, m, key, 8, [&](cudaStream_t cs) {
+          return enqueue_cycle(A, M, b, x, ws, m, true, nullptr, cs);
+        }));
       KKT_TRY_CUDA(cudaGraphLaunch(ws.graph.exec, s));
     } else {
       KKT_TRY(enqueue_cycle(A, M, b, x, ws, m, true, nullptr, s));
@@ -563,5 +567,203 @@ kkt_status gmres_run(Operator& A, Operator* M, const double* b, double* x, Gmres
   }
   res->relres = beta / bnorm;
   res->status = status;
+  return KKT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Several independent problems in lockstep (gmres_solve_batch).  Their
+// unknowns are concatenated (problem k from off[k]); V, Z, w, r hold all of
+// them, every problem has its own state, Hessenberg column and rotations.
+// Step j applies the preconditioner to all problems at once (the subdomain
+// solve over all boxes, each box gated by its problem's state), then each
+// problem's matvec, CGS2 and rotation on its own part, gated by its state.
+// ---------------------------------------------------------------------------
+kkt_status BatchWork::alloc(const std::vector<long long>& off_, int m_) {
+  if (off_ == off && m_ <= ws.m) return KKT_OK;
+  release();
+  off = off_;
+  const int np = (int)off.size() - 1;
+  KKT_TRY(ws.alloc(off.back(), m_, true));
+  if (cudaMalloc(&st, np * sizeof(GmresState)) != cudaSuccess ||
+      cudaMalloc(&small, (size_t)np * GmresWork::doubles(ws.m) * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&st_host, np * sizeof(GmresState)) != cudaSuccess ||
+      cudaMemset(st, 0, np * sizeof(GmresState)) != cudaSuccess ||
+      cudaMemset(small, 0, (size_t)np * GmresWork::doubles(ws.m) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    set_error("gmres_solve_batch: workspace allocation failed");
+    return KKT_ERR_NOMEM;
+  }
+  return KKT_OK;
+}
+
+void BatchWork::release() {
+  ws.release();
+  cudaFree(st);
+  cudaFree(small);
+  if (st_host) cudaFreeHost(st_host);
+  st = nullptr;
+  small = nullptr;
+  st_host = nullptr;
+  off.clear();
+}
+
+namespace {
+
+// the small arrays of problem k, laid out as in GmresWork
+struct Small {
+  double *h, *h2, *y, *cs, *sn, *g, *H;
+};
+Small small_of(const BatchWork& bw, int k) {
+  const int m = bw.ws.m;
+  double* b = bw.small + (size_t)k * GmresWork::doubles(m);
+  Small o;
+  o.h = b;
+  o.h2 = b + (m + 2);
+  o.y = b + 2 * (m + 2);
+  o.cs = o.y + m;
+  o.sn = o.cs + m;
+  o.g = o.sn + m;
+  o.H = o.g + (m + 1);
+  return o;
+}
+
+kkt_status enqueue_cycle_batch(std::vector<Operator*>& A, Operator& M, const double* b, double* x, BatchWork& bw,
+                               int m, cudaStream_t s) {
+  GmresWork& ws = bw.ws;
+  const long long N = ws.n;   // all problems
+  const int np = (int)bw.off.size() - 1;
+  for (int k = 0; k < np; ++k) {
+    gm_begin<<<1, 32, 0, s>>>(bw.st + k, small_of(bw, k).g, m, nullptr);
+    KKT_TRY(launched());
+    const long long o = bw.off[k];
+    scale_dev<<<kVecBlocks, 256, 0, s>>>(ws.V + o, ws.r + o, &bw.st[k].inv, bw.off[k + 1] - o, &bw.st[k].active);
+    KKT_TRY(launched());
+  }
+  constexpr int kStride = (int)(sizeof(GmresState) / sizeof(int));
+  for (int j = 0; j < m; ++j) {
+    if (g_capture) g_capture->step = j;
+    double* Vj = ws.V + (size_t)j * N;
+    double* Zj = ws.Z + (size_t)j * N;
+    // the preconditioner of every problem in one launch, boxes gated by their problem
+    KKT_TRY(M.apply(Vj, Zj, s, &bw.st[0].active));
+    static_assert(sizeof(GmresState) % sizeof(int) == 0, "state stride");
+    (void)kStride;
+    for (int k = 0; k < np; ++k) {
+      const long long o = bw.off[k], nk = bw.off[k + 1] - o;
+      const int* act = &bw.st[k].active;
+      const Small sm = small_of(bw, k);
+      KKT_TRY(A[k]->apply(Zj + o, ws.w + o, s, act));
+      KKT_TRY(multidot(ws.V + o, N, j + 1, ws.w + o, nk, ws.part, sm.h, s, act));
+      multi_axpy<<<kVecBlocks, 256, 0, s>>>(ws.w + o, ws.V + o, N, sm.h, j + 1, nk, act);
+      KKT_TRY(launched());
+      KKT_TRY(multidot(ws.V + o, N, j + 1, ws.w + o, nk, ws.part, sm.h2, s, act));
+      multi_axpy<<<kVecBlocks, 256, 0, s>>>(ws.w + o, ws.V + o, N, sm.h2, j + 1, nk, act);
+      KKT_TRY(launched());
+      KKT_TRY(multidot(ws.w + o, 0, 1, ws.w + o, nk, ws.part, sm.h + j + 1, s, act));
+      gm_givens<<<1, 32, 0, s>>>(bw.st + k, j, m, sm.h, sm.h2, sm.H, sm.cs, sm.sn, sm.g);
+      KKT_TRY(launched());
+      if (j + 1 < m) {
+        scale_dev<<<kVecBlocks, 256, 0, s>>>(ws.V + (size_t)(j + 1) * N + o, ws.w + o, &bw.st[k].inv, nk, act);
+        KKT_TRY(launched());
+      }
+    }
+  }
+  if (g_capture) g_capture->step = -1;
+  for (int k = 0; k < np; ++k) {
+    const long long o = bw.off[k], nk = bw.off[k + 1] - o;
+    const Small sm = small_of(bw, k);
+    gm_solve_y<<<1, 32, 0, s>>>(bw.st + k, m, sm.H, sm.g, sm.y);
+    KKT_TRY(launched());
+    multi_update<<<kVecBlocks, 256, 0, s>>>(x + o, ws.Z + o, N, sm.y, &bw.st[k].k, nk, &bw.st[k].ran);
+    KKT_TRY(launched());
+    // true residual of problem k and its squared norm
+    KKT_TRY(A[k]->apply(x + o, ws.w + o, s, nullptr));
+    KKT_TRY(vec_copy(ws.r + o, b + o, nk, s));
+    KKT_TRY(vec_axpby(ws.r + o, -1.0, ws.w + o, 1.0, nk, s));
+    KKT_TRY(multidot(ws.r + o, 0, 1, ws.r + o, nk, ws.part, &bw.st[k].r2, s, nullptr));
+  }
+  return KKT_OK;
+}
+
+}  // namespace
+
+kkt_status gmres_run_batch(std::vector<Operator*>& A, Operator& M, const double* b, double* x, BatchWork& bw,
+                           int restart, double rtol, int maxit, std::vector<GmresResult>& res, cudaStream_t s,
+                           bool graph) {
+  GmresWork& ws = bw.ws;
+  const int np = (int)bw.off.size() - 1;
+  const int m = restart;
+  if (m > ws.m || (int)A.size() != np) {
+    set_error("gmres_solve_batch: restart longer than the workspace or operator count mismatch");
+    return KKT_ERR_ARG;
+  }
+  res.assign(np, GmresResult{});
+  // ||b_k||, zero guess: r = b
+  KKT_TRY(vec_zero(x, ws.n, s));
+  KKT_TRY(vec_copy(ws.r, b, ws.n, s));
+  for (int k = 0; k < np; ++k) {
+    const long long o = bw.off[k], nk = bw.off[k + 1] - o;
+    KKT_TRY(multidot(b + o, 0, 1, b + o, nk, ws.part, &bw.st[k].b2, s, nullptr));
+    KKT_TRY(multidot(b + o, 0, 1, b + o, nk, ws.part, &bw.st[k].r2, s, nullptr));
+    gm_init<<<1, 32, 0, s>>>(bw.st + k, rtol, maxit, nullptr);
+    KKT_TRY(launched());
+  }
+  KKT_TRY_CUDA(cudaMemcpyAsync(bw.st_host, bw.st, np * sizeof(GmresState), cudaMemcpyDeviceToHost, s));
+  KKT_TRY_CUDA(cudaStreamSynchronize(s));
+  std::vector<char> done(np, 0);
+  for (int k = 0; k < np; ++k) {
+    const double bn = bw.st_host[k].bnorm;
+    if (!std::isfinite(bn)) {
+      res[k].status = KKT_ERR_NONFINITE;
+      done[k] = 1;
+    } else if (bn == 0.0) {
+      res[k].status = KKT_OK;
+      done[k] = 1;
+    }
+  }
+  unsigned long long key[10] = {M.uid(), (unsigned long long)(uintptr_t)b, (unsigned long long)(uintptr_t)x,
+                                (unsigned long long)m, (unsigned long long)g_timing_on.load(),
+                                (unsigned long long)(uintptr_t)ws.V, (unsigned long long)np, 2ull, 0ull, 0ull};
+  for (int k = 0; k < np; ++k) key[8] = key[8] * 1000003ull + A[k]->uid();
+  for (;;) {
+    bool any = false;
+    for (int k = 0; k < np; ++k) any = any || !done[k];
+    if (!any) break;
+    if (graph) {
+      if (!ws.graph.exec || std::memcmp(ws.graph.key, key, sizeof(key)) != 0)
+        KKT_TRY(capture_cycle(ws, m, key, 2 * np + 2, [&](cudaStream_t cs) {
+          return enqueue_cycle_batch(A, M, b, x, bw, m, cs);
+        }));
+      KKT_TRY_CUDA(cudaGraphLaunch(ws.graph.exec, s));
+    } else {
+      KKT_TRY(enqueue_cycle_batch(A, M, b, x, bw, m, s));
+    }
+    KKT_TRY_CUDA(cudaMemcpyAsync(bw.st_host, bw.st, np * sizeof(GmresState), cudaMemcpyDeviceToHost, s));
+    KKT_TRY_CUDA(cudaStreamSynchronize(s));
+    int steps = 0;
+    for (int k = 0; k < np; ++k) steps = std::max(steps, bw.st_host[k].steps);
+    if (graph) KKT_TRY(after_replay(ws.graph, steps));
+    for (int k = 0; k < np; ++k) {
+      if (done[k]) continue;
+      const GmresState& h = bw.st_host[k];
+      const double beta = std::sqrt(h.r2);
+      res[k].iters = h.iters;
+      res[k].relres = beta / h.bnorm;
+      if (h.flag == kGmNonFinite || !std::isfinite(beta)) {
+        res[k].status = KKT_ERR_NONFINITE;
+        done[k] = 1;
+      } else if (beta <= rtol * h.bnorm) {
+        res[k].status = KKT_OK;
+        done[k] = 1;
+      } else if (h.flag == kGmBreakdown) {
+        res[k].status = KKT_BREAKDOWN;
+        done[k] = 1;
+      } else if (h.iters >= maxit || h.steps == 0) {
+        res[k].status = KKT_NOT_CONVERGED;
+        done[k] = 1;
+      }
+    }
+  }
   return KKT_OK;
 }

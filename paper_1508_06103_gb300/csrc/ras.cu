@@ -52,6 +52,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -329,9 +330,10 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
     const BoxDesc* __restrict__ boxes, const Chunk* __restrict__ chunks, const S* __restrict__ F,
     typename SolveArith<S>::type* __restrict__ V, const double* __restrict__ r, double* __restrict__ z,
     const int2* __restrict__ gtab, const int2* __restrict__ otab, const int* __restrict__ vtab, int bstride,
-    int nstage, int* __restrict__ status, const int* gate) {
+    int nstage, int* __restrict__ status, const int* gate, int gate_stride) {
   using T = typename SolveArith<S>::type;
-  if (gated_off(gate)) return;
+  // the box's problem gate (one problem: gate_stride 0, every box reads gate[0])
+  if (gate != nullptr && gate[boxes[blockIdx.x].prob * gate_stride] == 0) return;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 1536);
   int* abort_at = reinterpret_cast<int*>(smem + 1536 + 8 * kMaxStages);   // block whose wait gave up, or -1
@@ -606,19 +608,31 @@ kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, const ShapeR
 
 }  // namespace
 
-kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
-                      const int* shape, ras_precond** out) {
-  if (!p || !nsub || !out) {
-    set_error("ras_setup: null argument");
+kkt_status ras_create(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap, int local,
+                      int factor_prec, const int* shape, ras_precond** out) {
+  if (!probs || nprob < 1 || !nsub || !out) {
+    set_error("ras_setup: null argument or no problem");
     return KKT_ERR_ARG;
   }
   *out = nullptr;
-  const int dims[4] = {p->nx, p->ny, p->nz, p->L};
-  for (int a = 0; a < 4; ++a)
-    if (nsub[a] < 1 || nsub[a] > dims[a]) {
-      set_error("ras_setup: each nsub must lie in [1, points along that axis]");
+  for (int k = 0; k < nprob; ++k) {
+    const kkt_problem* pk = probs[k];
+    if (!pk) {
+      set_error("ras_setup: null problem");
       return KKT_ERR_ARG;
     }
+    const int dk[4] = {pk->nx, pk->ny, pk->nz, pk->L};
+    for (int a = 0; a < 4; ++a)
+      if (nsub[a] < 1 || nsub[a] > dk[a]) {
+        set_error("ras_setup: each nsub must lie in [1, points along that axis]");
+        return KKT_ERR_ARG;
+      }
+  }
+  if (nprob > 1 && local != 0) {
+    set_error("ras_setup_batch: the subdomains of several problems use ILU(0) local solves");
+    return KKT_ERR_ARG;
+  }
+  kkt_problem* p = probs[0];
   if (overlap < 0 || (local != 0 && local != 1) || (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
     set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)) or 1 (exact LU), factor_prec 64, 32 or 16");
     return KKT_ERR_ARG;
@@ -653,19 +667,50 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   ras_precond* m = new (std::nothrow) ras_precond();
   if (!m) return KKT_ERR_NOMEM;
   m->prob = p;
+  m->probs.assign(probs, probs + nprob);
+  m->vec_off.assign(1, 0);
+  for (int k = 0; k < nprob; ++k) m->vec_off.push_back(m->vec_off.back() + probs[k]->n);
+  m->n_total = m->vec_off.back();
   m->prec = factor_prec;
   m->local = local;
   auto stride = [&](int n) { return chunk_stride_of(factor_prec, n); };
-  std::vector<std::pair<int, int>> pr[4];
-  for (int a = 0; a < 4; ++a) pr[a] = parts(dims[a], nsub[a]);
+  // every box: its problem and the owned part of each axis (part k of n holds
+  // floor(n/p) + (k < n mod p)); the extended box adds `overlap`, trimmed
+  struct Geom {
+    int prob;
+    std::pair<int, int> own[4];
+    long long points;
+  };
+  std::vector<Geom> geoms;
+  for (int k = 0; k < nprob; ++k) {
+    const kkt_problem* pk = probs[k];
+    const int dk[4] = {pk->nx, pk->ny, pk->nz, pk->L};
+    std::vector<std::pair<int, int>> prk[4];
+    for (int a = 0; a < 4; ++a) prk[a] = parts(dk[a], nsub[a]);
+    for (int it = 0; it < nsub[3]; ++it)
+      for (int iz = 0; iz < nsub[2]; ++iz)
+        for (int iy = 0; iy < nsub[1]; ++iy)
+          for (int ix = 0; ix < nsub[0]; ++ix) {
+            Geom g{k, {prk[0][ix], prk[1][iy], prk[2][iz], prk[3][it]}, 1};
+            for (int a = 0; a < 4; ++a)
+              g.points *= std::min(dk[a], g.own[a].second + overlap) - std::max(0, g.own[a].first - overlap);
+            geoms.push_back(g);
+          }
+  }
+  // several problems: the largest boxes first, so that the CTAs of one launch
+  // (one per box, started in list order) finish as close together as they can
+  if (nprob > 1)
+    std::stable_sort(geoms.begin(), geoms.end(), [](const Geom& a, const Geom& b) { return a.points > b.points; });
   {
-    // largest padded local vector: boxes are products of one part per axis
-    long long pad = kVecWidth;
-    for (int a = 0; a < 4; ++a) {
-      int mx = 0;
-      for (const auto& q : pr[a])
-        mx = std::max(mx, std::min(dims[a], q.second + overlap) - std::max(0, q.first - overlap));
-      pad *= mx + 2;
+    // largest padded local vector
+    long long pad = 0;
+    for (const Geom& g : geoms) {
+      const kkt_problem* pk = probs[g.prob];
+      const int dk[4] = {pk->nx, pk->ny, pk->nz, pk->L};
+      long long v = kVecWidth;
+      for (int a = 0; a < 4; ++a)
+        v *= std::min(dk[a], g.own[a].second + overlap) - std::max(0, g.own[a].first - overlap) + 2;
+      pad = std::max(pad, v);
     }
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -675,7 +720,7 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       delete m;
       return KKT_ERR_CUDA;
     }
-    const int nbox = nsub[0] * nsub[1] * nsub[2] * nsub[3];
+    const int nbox = (int)geoms.size();
     ShapeRequest req;
     if (shape) {
       req.ch = shape[0];
@@ -702,19 +747,20 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
   std::vector<int> perm, iperm, lptr;
   std::vector<int2> ptab, gtab, otab;
   std::vector<int> vtab;
-  if (3LL * p->P >= INT32_MAX) {
+  if (m->n_total >= INT32_MAX) {
     set_error("ras_setup: more than 2^31 unknowns are not supported");
     delete m;
     return KKT_ERR_ARG;
   }
   std::vector<Chunk> chunks;
   long long foff = 0, voff = 0;
-  for (int it = 0; it < nsub[3]; ++it)
-    for (int iz = 0; iz < nsub[2]; ++iz)
-      for (int iy = 0; iy < nsub[1]; ++iy)
-        for (int ix = 0; ix < nsub[0]; ++ix) {
+  for (const Geom& geo : geoms) {
+          const kkt_problem* pk = probs[geo.prob];
+          const long long gbase = m->vec_off[geo.prob];   // the problem's first unknown
+          const int dims[4] = {pk->nx, pk->ny, pk->nz, pk->L};
           BoxDesc b{};
-          const std::pair<int, int>* own[4] = {&pr[0][ix], &pr[1][iy], &pr[2][iz], &pr[3][it]};
+          b.prob = geo.prob;
+          const std::pair<int, int>* own[4] = {&geo.own[0], &geo.own[1], &geo.own[2], &geo.own[3]};
           int lo[4], hi[4];
           for (int a = 0; a < 4; ++a) {
             lo[a] = std::max(0, own[a]->first - overlap);
@@ -760,8 +806,8 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
               return (int)(kVecWidth * ((kx + 1) + sy * (ky + 1) + sz * (kz + 1) + st * (kt + 1)));
             };
             auto glob = [&](int kx, int ky, int kz, int kt) {
-              return (int)(3 * ((long long)(b.t0 + kt) * p->N + (b.x0 + kx) +
-                                (long long)p->nx * ((b.y0 + ky) + (long long)p->ny * (b.z0 + kz))));
+              return (int)(gbase + 3 * ((long long)(b.t0 + kt) * pk->N + (b.x0 + kx) +
+                                        (long long)pk->nx * ((b.y0 + ky) + (long long)pk->ny * (b.z0 + kz))));
             };
             const size_t g0 = gtab.size();
             gtab.resize(g0 + b.P);
@@ -866,8 +912,10 @@ kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local,
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
       cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * vsz) != cudaSuccess ||
       (factor_prec == 16 && cudaMalloc(&m->Ffac, foff * sizeof(float)) != cudaSuccess) ||
-      cudaMalloc(&m->status, sizeof(int)) != cudaSuccess)
+      cudaMalloc(&m->status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&m->dprobs, m->probs.size() * sizeof(DevProblem)) != cudaSuccess)
     return fail(KKT_ERR_NOMEM, "device allocation failed");
+  m->dprobs_h.resize(m->probs.size());
   if (local == 1) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(KKT_ERR_CUDA, "cudaMemGetInfo failed");
@@ -913,7 +961,7 @@ namespace {
 
 template <typename S>
 kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename SolveArith<S>::type* V,
-                        cudaStream_t s, const int* gate = nullptr) {
+                        cudaStream_t s, const int* gate = nullptr, int gate_stride = 0) {
   using T = typename SolveArith<S>::type;
   const int threads = (m->ch * kLanes + 31) / 32 * 32;
   const int bstride = kLRanks * m->cpmax;
@@ -921,10 +969,12 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename Sol
   const size_t smem = solve_smem(m->cpmax, m->nstage, sizeof(S), sizeof(T), m->max_pad, m->smem_vec);
   if (m->smem_vec)
     ras_solve<S, true><<<m->nbox, threads, smem, s>>>(m->boxes, m->chunks, (const S*)m->F, V, r, z, m->gtab,
-                                                      m->otab, m->vtab, bstride, m->nstage, m->status, gate);
+                                                      m->otab, m->vtab, bstride, m->nstage, m->status, gate,
+                                                      gate_stride);
   else
     ras_solve<S, false><<<m->nbox, threads, smem, s>>>(m->boxes, m->chunks, (const S*)m->F, V, r, z, m->gtab,
-                                                       m->otab, m->vtab, bstride, m->nstage, m->status, gate);
+                                                       m->otab, m->vtab, bstride, m->nstage, m->status, gate,
+                                                       gate_stride);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   return KKT_OK;
@@ -934,6 +984,10 @@ kkt_status launch_solve(ras_precond* m, const double* r, double* z, typename Sol
 
 kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s) {
   KKT_TRY_CUDA(cudaMemsetAsync(m->status, 0, sizeof(int), s));
+  // the problems as the value gather reads them now (the regularisation may have changed)
+  for (size_t k = 0; k < m->probs.size(); ++k) m->dprobs_h[k] = m->probs[k]->dev();
+  KKT_TRY_CUDA(cudaMemcpyAsync(m->dprobs, m->dprobs_h.data(), m->dprobs_h.size() * sizeof(DevProblem),
+                               cudaMemcpyHostToDevice, s));
   if (m->local == 1) KKT_TRY(ras_lu_factor(m, s));
   else if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
   else if (m->prec == 32) KKT_TRY(ras_factor_launch32(m, s));
@@ -957,12 +1011,13 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
   return ras_factor_status(m);
 }
 
-kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate) {
+kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate,
+                      int gate_stride) {
   TimedScope timed(&m->timing, s);
   if (m->local == 1) return ras_lu_solve(m, r, z, s, gate);
-  if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s, gate);
-  if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s, gate);
-  return launch_solve<__nv_bfloat16>(m, r, z, (float*)m->V, s, gate);
+  if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s, gate, gate_stride);
+  if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s, gate, gate_stride);
+  return launch_solve<__nv_bfloat16>(m, r, z, (float*)m->V, s, gate, gate_stride);
 }
 
 kkt_status ras_check(ras_precond* m) {
@@ -977,7 +1032,7 @@ kkt_status ras_check(ras_precond* m) {
 
 extern "C" kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
                                 ras_precond** out) {
-  return ras_create(p, nsub, overlap, local, factor_prec, nullptr, out);
+  return ras_create(&p, 1, nsub, overlap, local, factor_prec, nullptr, out);
 }
 
 extern "C" kkt_status ras_setup_shape(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
@@ -992,7 +1047,18 @@ extern "C" kkt_status ras_setup_shape(kkt_problem* p, const int nsub[4], int ove
               "vector placement 0, 1 or 2}");
     return KKT_ERR_ARG;
   }
-  return ras_create(p, nsub, overlap, local, factor_prec, shape, out);
+  return ras_create(&p, 1, nsub, overlap, local, factor_prec, shape, out);
+}
+
+extern "C" kkt_status ras_setup_batch(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap,
+                                      int factor_prec, const int shape[4], ras_precond** out) {
+  if (shape && (shape[0] < 0 || shape[1] < 0 || (shape[1] != 0 && (shape[1] < 2 || shape[1] > kMaxStages)) ||
+                (shape[2] != 0 && shape[2] != kLanes) || shape[3] < 0 || shape[3] > 2)) {
+    set_error("ras_setup_batch: shape = {chunk points >= 0, ring buffers 0 or 2..4, lanes 0 or 4, "
+              "vector placement 0, 1 or 2}");
+    return KKT_ERR_ARG;
+  }
+  return ras_create(probs, nprob, nsub, overlap, 0, factor_prec, shape, out);
 }
 
 extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream) {
@@ -1000,7 +1066,7 @@ extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void
     set_error("ras_apply: null argument");
     return KKT_ERR_ARG;
   }
-  if (spans_overlap(r, z, m->prob->n)) {
+  if (spans_overlap(r, z, m->n_total)) {
     set_error("ras_apply: r and z must not overlap");
     return KKT_ERR_ARG;
   }
@@ -1114,6 +1180,8 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->F);
   cudaFree(m->V);
   cudaFree(m->status);
+  cudaFree(m->dprobs);
+  delete m->bw;
   delete m;
 }
 
@@ -1159,7 +1227,7 @@ extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* 
     set_error("ras_apply_static: null argument");
     return KKT_ERR_ARG;
   }
-  if (spans_overlap(r, z, m->prob->n)) {
+  if (spans_overlap(r, z, m->n_total)) {
     set_error("ras_apply_static: r and z must not overlap");
     return KKT_ERR_ARG;
   }
@@ -1187,4 +1255,143 @@ extern "C" kkt_status ras_apply_static(ras_precond* m, const double* r, double* 
   if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)scratch, s);
   if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)scratch, s);
   return launch_solve<__nv_bfloat16>(m, r, z, (float*)scratch, s);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the subdomain solve's shape: every compiled chunk size with
+// 2 and 3 copy buffers (local vectors placed as the chooser places them) is
+// set up on the given problems and timed over `reps` applies with CUDA
+// events; the fastest is returned and, with a cache file, remembered there
+// under a key of the problems' sizes, the split, the precision and the
+// device, one line per key ("key<TAB>chunk stages ms").
+// ---------------------------------------------------------------------------
+namespace {
+
+std::string tune_key(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap, int prec) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string k = std::string(prop.name) + ";prec=" + std::to_string(prec) + ";ov=" + std::to_string(overlap) +
+                  ";nsub=" + std::to_string(nsub[0]) + "," + std::to_string(nsub[1]) + "," + std::to_string(nsub[2]) +
+                  "," + std::to_string(nsub[3]) + ";";
+  for (int i = 0; i < nprob; ++i)
+    k += std::to_string(probs[i]->nx) + "x" + std::to_string(probs[i]->ny) + "x" + std::to_string(probs[i]->nz) +
+         "x" + std::to_string(probs[i]->L) + (i + 1 < nprob ? "," : "");
+  for (char& c : k)
+    if (c == '\t' || c == '\n') c = ' ';
+  return k;
+}
+
+__global__ void fill_ones(double* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = 1.0;
+}
+
+}  // namespace
+
+extern "C" kkt_status ras_autotune(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap,
+                                   int factor_prec, int reps, const char* cache_path, int shape_out[4],
+                                   double* best_ms) {
+  if (!probs || nprob < 1 || !nsub || !shape_out || reps < 1 ||
+      (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
+    set_error("ras_autotune: bad argument");
+    return KKT_ERR_ARG;
+  }
+  const std::string key = tune_key(probs, nprob, nsub, overlap, factor_prec);
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[4096];
+      while (std::fgets(line, sizeof(line), f)) {
+        char* tab = std::strchr(line, '\t');
+        if (!tab || std::string(line, tab) != key) continue;
+        int ch = 0, ns = 0;
+        double ms = 0.0;
+        if (std::sscanf(tab + 1, "%d %d %lf", &ch, &ns, &ms) == 3) {
+          std::fclose(f);
+          shape_out[0] = ch;
+          shape_out[1] = ns;
+          shape_out[2] = kLanes;
+          shape_out[3] = 0;
+          if (best_ms) *best_ms = ms;
+          return KKT_OK;
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  int cands[3] = {ChunkCfg<float>::CH, ChunkCfg<float>::CH2, ChunkCfg<float>::CH3};
+  if (factor_prec == 64) {
+    cands[0] = ChunkCfg<double>::CH;
+    cands[1] = ChunkCfg<double>::CH2;
+    cands[2] = ChunkCfg<double>::CH3;
+  } else if (factor_prec == 16) {
+    cands[0] = ChunkCfg<__nv_bfloat16>::CH;
+    cands[1] = ChunkCfg<__nv_bfloat16>::CH2;
+    cands[2] = ChunkCfg<__nv_bfloat16>::CH3;
+  }
+  long long n = 0;
+  for (int i = 0; i < nprob; ++i) n += probs[i]->n;
+  double *r = nullptr, *z = nullptr;
+  if (cudaMalloc(&r, n * sizeof(double)) != cudaSuccess || cudaMalloc(&z, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(r);
+    set_error("ras_autotune: device allocation failed");
+    return KKT_ERR_NOMEM;
+  }
+  fill_ones<<<1216, 256>>>(r, n);
+  KKT_COUNT(1);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = -1.0;
+  int best_ch = 0, best_ns = 0;
+  kkt_status err = KKT_OK;
+  for (int ci = 0; ci < 3 && err == KKT_OK; ++ci)
+    for (int ns = 2; ns <= 3 && err == KKT_OK; ++ns) {
+      const int shape[4] = {cands[ci], ns, 0, 0};
+      ras_precond* m = nullptr;
+      const kkt_status st = ras_create(probs, nprob, nsub, overlap, 0, factor_prec, shape, &m);
+      if (st == KKT_ERR_ARG) continue;   // this shape does not fit the device
+      if (st != KKT_OK) {
+        err = st;
+        break;
+      }
+      kkt_status ls = ras_launch(m, r, z, nullptr);   // warm-up
+      cudaEventRecord(e0, nullptr);
+      for (int i = 0; i < reps && ls == KKT_OK; ++i) ls = ras_launch(m, r, z, nullptr);
+      cudaEventRecord(e1, nullptr);
+      float ms = 0.f;
+      if (ls == KKT_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        const double per = ms / reps;
+        if (best < 0 || per < best) {
+          best = per;
+          best_ch = cands[ci];
+          best_ns = ns;
+        }
+      } else if (ls != KKT_OK) {
+        err = ls;
+      }
+      ras_destroy(m);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(r);
+  cudaFree(z);
+  if (err != KKT_OK) return err;
+  if (best < 0) {
+    set_error("ras_autotune: no shape of the subdomain solve fits these subdomains");
+    return KKT_ERR_ARG;
+  }
+  shape_out[0] = best_ch;
+  shape_out[1] = best_ns;
+  shape_out[2] = kLanes;
+  shape_out[3] = 0;
+  if (best_ms) *best_ms = best;
+  if (cache_path)
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s\t%d %d %.6f\n", key.c_str(), best_ch, best_ns, best);
+      std::fclose(f);
+    }
+  return KKT_OK;
 }

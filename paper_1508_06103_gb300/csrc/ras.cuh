@@ -34,6 +34,7 @@ struct BoxDesc {
   int nown;                    // owned points
   long long ooff;              // offset into the owned-point table
   int kl;                      // exact LU: half-bandwidth of the box matrix
+  int prob;                    // problem of the box (a preconditioner over several problems)
   long long aoff;              // exact LU: offset of the box's band (elements)
 };
 
@@ -44,7 +45,14 @@ constexpr int kMaxLuUnknowns = 28672;
 
 struct ras_precond {
   unsigned long long uid = next_handle_uid();
-  kkt_problem* prob = nullptr;
+  kkt_problem* prob = nullptr;           // the (first) problem
+  // problems of the boxes: one, or several solved together (ras_setup_batch); their
+  // unknowns are concatenated in that order, problem k from vec_off[k]
+  std::vector<kkt_problem*> probs;
+  std::vector<long long> vec_off;        // nprob + 1 offsets
+  long long n_total = 0;
+  DevProblem* dprobs = nullptr;          // device copies of the problems' DevProblem
+  std::vector<DevProblem> dprobs_h;
   int prec = 64;               // factor storage: 64, 32, or 16 (BF16; factorisation and solve in FP32)
   int nbox = 0;
   int ch = 0;                  // points per chunk of the subdomain solve (chosen per preconditioner)
@@ -79,12 +87,15 @@ struct ras_precond {
   int lu_ctas = 1;             // exact LU: CTAs per box in an elimination step
   TimingLog timing;            // subdomain-solve launches
   TimingLog factor_timing;     // ILU(0) factorisation launches
+  BatchWork* bw = nullptr;     // gmres_solve_batch workspace (several problems)
 };
 
 // shape: NULL, or {chunk points, ring buffers, lanes per point, vector placement
-// (1 shared, 2 global)} of the subdomain solve, 0 = chosen automatically
-kkt_status ras_create(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
-                      const int* shape, ras_precond** out);
+// (1 shared, 2 global)} of the subdomain solve, 0 = chosen automatically.
+// Several problems: every problem is split by nsub and all boxes form one list,
+// largest first (so the CTAs of a launch finish together as far as they can).
+kkt_status ras_create(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap, int local,
+                      int factor_prec, const int* shape, ras_precond** out);
 kkt_status ras_factor(ras_precond* m, cudaStream_t s);          // enqueue, synchronise, check
 kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s);  // enqueue only
 kkt_status ras_factor_status(ras_precond* m);                   // after the stream completed
@@ -96,5 +107,8 @@ kkt_status ras_factor_launch16(ras_precond* m, cudaStream_t s);   // FP32 factor
 kkt_status ras_lu_factor(ras_precond* m, cudaStream_t s);
 kkt_status ras_lu_solve(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate);
 // the subdomain solve z = M^{-1} r on s; its kernel returns at once while *gate reads 0
-kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate = nullptr);
+// gate_stride: distance (ints) between the gates of consecutive problems; box b
+// reads gate[prob(b) * gate_stride]
+kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate = nullptr,
+                      int gate_stride = 0);
 kkt_status ras_check(ras_precond* m);

@@ -200,6 +200,17 @@ kkt_status two_level(coarse_level* c, ras_precond* fine, const double* x, double
   return KKT_OK;
 }
 
+// The one-level RAS of several problems: one subdomain solve over all their
+// boxes, box b gated by its problem's FGMRES state.
+struct BatchRasOp : Operator {
+  ras_precond* m;
+  explicit BatchRasOp(ras_precond* m_) : m(m_) {}
+  kkt_status apply(const double* x, double* y, cudaStream_t s, const int* gate) override {
+    return ras_launch(m, x, y, s, gate, gate ? (int)(sizeof(GmresState) / sizeof(int)) : 0);
+  }
+  unsigned long long uid() const override { return m->uid; }
+};
+
 struct TwoLevelOp : Operator {
   coarse_level* c;
   ras_precond* fine;
@@ -262,7 +273,7 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
   kkt_status st = create_problem(&cg, cnt, fine->tau * c->rt, ac.data(), vc.data(), sc.empty() ? nullptr : sc.data(),
                                  (int)sc.size(), fine->beta1, fine->beta2, fine->theta, &c->cp);
   if (st == KKT_OK) c->cp->reg = fine->reg;   // the coarse operator is the same discretisation
-  if (st == KKT_OK) st = ras_create(c->cp, nsub_c, c_overlap, 0, factor_prec, nullptr, &c->cras);
+  if (st == KKT_OK) st = ras_create(&c->cp, 1, nsub_c, c_overlap, 0, factor_prec, nullptr, &c->cras);
   // The coarse GMRES keeps z_j = M_c^{-1} v_j (the flexible form's store, c_maxit
   // coarse vectors) and forms y_c = Z y: for its fixed preconditioner this is
   // the right-preconditioned iterate M_c^{-1} V y with one application less.
@@ -383,4 +394,47 @@ extern "C" kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* 
   if (iters) *iters = res.iters;
   if (true_relres) *true_relres = res.relres;
   return res.status;
+}
+
+extern "C" kkt_status gmres_solve_batch(kkt_problem* const* probs, int nprob, ras_precond* m, const double* b,
+                                        double* x, int restart, double rtol, int maxit, int* iters,
+                                        double* true_relres, int* status, void* stream) {
+  if (!probs || nprob < 1 || !m || !b || !x || restart < 1 || maxit < 0 || !(rtol > 0)) {
+    set_error("gmres_solve_batch: bad argument");
+    return KKT_ERR_ARG;
+  }
+  if ((int)m->probs.size() != nprob || !std::equal(m->probs.begin(), m->probs.end(), probs)) {
+    set_error("gmres_solve_batch: the preconditioner was set up for another list of problems");
+    return KKT_ERR_ARG;
+  }
+  if (spans_overlap(b, x, m->n_total)) {
+    set_error("gmres_solve_batch: b and x must not overlap");
+    return KKT_ERR_ARG;
+  }
+  if (!m->bw) {
+    m->bw = new (std::nothrow) BatchWork();
+    if (!m->bw) return KKT_ERR_NOMEM;
+  }
+  KKT_TRY(m->bw->alloc(m->vec_off, restart));
+  std::vector<KktOp> ops;
+  ops.reserve(nprob);
+  std::vector<Operator*> A;
+  for (int k = 0; k < nprob; ++k) {
+    ops.emplace_back(probs[k]);
+    A.push_back(&ops.back());
+  }
+  BatchRasOp M(m);
+  std::vector<GmresResult> res;
+  KKT_TRY(gmres_run_batch(A, M, b, x, *m->bw, restart, rtol, maxit, res, (cudaStream_t)stream, true));
+  KKT_TRY(ras_check(m));
+  kkt_status worst = KKT_OK;
+  for (int k = 0; k < nprob; ++k) {
+    if (iters) iters[k] = res[k].iters;
+    if (true_relres) true_relres[k] = res[k].relres;
+    if (status) status[k] = res[k].status;
+    if (res[k].status < 0 && (worst >= 0 || res[k].status < worst)) worst = res[k].status;
+    else if (worst >= 0 && res[k].status > worst) worst = res[k].status;
+  }
+  if (worst < 0) set_error("gmres_solve_batch: a problem met a non-finite value");
+  return worst;
 }

@@ -274,6 +274,41 @@ def large() -> Workload:
     )
 
 
+def batch(seed: int = 4, count: int = 8) -> List[Workload]:
+    """Independent inverse problems solved together (one launch per kernel for all of them).
+
+    Each member is drawn from `seed`: a grid of c^3 cells with c in [16, 40] and M in [32, 80]
+    Crank-Nicolson steps, an m^3 sensor lattice with m in [3, 6], noise of 0.5-5 %, and 1-3
+    Gaussian sources on circular paths at seeded heights; a(x) = 0.05 + 0.05 rho(x) with rho a
+    seeded smooth field, v = (1, 1, 0) sin(pi z), Dirichlet on x = 0, beta scaled with h^2 from
+    1e-3 at 32 cells (as the 32^3 x 64 family).  Each problem is split into 4 x 4 x 2 x 2
+    space-time subdomains with overlap 1 (64 per problem, 512 for eight), FP32 local solves.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    L = (1.0, 1.0, 1.0)
+    for k in range(count):
+        c = int(rng.integers(16, 41))
+        M = int(rng.integers(32, 81))
+        m = int(rng.integers(3, 7))
+        eps = float(rng.uniform(0.005, 0.05))
+        nsrc = int(rng.integers(1, 4))
+        zs = rng.uniform(0.3, 0.7, nsrc)
+        cells = (c, c, c)
+        cen = cell_centroids(cells, L)
+        a = 0.05 + 0.05 * smooth_random_field(cen, seed=seed * 100 + k)
+        v = np.stack([np.sin(math.pi * cen[:, 2]), np.sin(math.pi * cen[:, 2]), np.zeros(len(cen))], axis=1)
+        beta = 1e-3 * (32.0 / c) ** 2
+        srcs = [Source(center=circular_path(i, nsrc, 1.0, float(z))) for i, z in enumerate(zs)]
+        out.append(Workload(
+            name=f"batch{seed}_{k}_{c}x{c}x{c}x{M}", cells=cells, lengths=L, T=1.0, M=M, theta=0.5,
+            dirichlet_faces=FACE_X0, a_cell=a, v_cell=v, sensor_xyz=sensor_lattice(m, L),
+            beta1=beta / 100, beta2=beta, sources=srcs, noise_eps=eps, noise_seed=seed * 100 + k,
+            nsub=(4, 4, 2, 2), overlap=1, local="ilu0", restart=30, rtol=1e-8,
+        ))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # the paper's Examples 1-3 (Sec. 4.1) as synthetic workloads
 # ---------------------------------------------------------------------------

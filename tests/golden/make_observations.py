@@ -12,6 +12,7 @@ outside its CPU-baseline leg.
     python tests/golden/make_observations.py              # observations_mid_32x32x32x64.txt
     python tests/golden/make_observations.py --refine 2   # ..._refined2.txt (not used by default)
     python tests/golden/make_observations.py --workload large   # observations_large_64x64x64x128.txt
+    python tests/golden/make_observations.py --workload batch   # observations_batch4_<k>_*.txt, 8 problems
 """
 
 import os
@@ -47,8 +48,14 @@ if __name__ == "__main__":
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--refine", type=int, default=1)
-    ap.add_argument("--workload", choices=["mid", "large"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "large", "batch"], default="mid")
     a = ap.parse_args()
+    if a.workload == "batch":
+        for wk in W.batch():
+            # iterative steps above ~25^3 nodes, where sparse LU fill grows large
+            write(wk, os.path.join(HERE, f"observations_{wk.name}.txt"), 1,
+                  "lu" if wk.cells[0] <= 24 else "bicgstab")
+        sys.exit(0)
     w = W.mid() if a.workload == "mid" else W.large()
     suffix = "" if a.refine == 1 else f"_refined{a.refine}"
     # the 65^3-node step matrix is too large for sparse LU: iterative steps to 1e-13

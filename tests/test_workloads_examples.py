@@ -52,3 +52,16 @@ def test_reduced_example1_marches_to_finite_data():
     obs = forward.observations(p, C, w.noise(), w.noise_eps)
     assert obs.shape == (9, 14 ** 3) and np.all(np.isfinite(obs)) and obs.max() > 0
     assert np.all(C[:, p.dirichlet] == 0.0)
+
+
+def test_batch_members_are_seeded_and_in_range():
+    a, b = W.batch(), W.batch()
+    assert len(a) == 8 and [w.name for w in a] == [w.name for w in b]
+    boxes = 0
+    for w in a:
+        assert 16 <= w.cells[0] <= 40 and w.cells[0] == w.cells[1] == w.cells[2] and 32 <= w.M <= 80
+        assert round(len(w.sensor_xyz) ** (1 / 3)) ** 3 == len(w.sensor_xyz) and 27 <= len(w.sensor_xyz) <= 216
+        assert 0.005 <= w.noise_eps <= 0.05 and 1 <= len(w.sources) <= 3
+        assert np.allclose(w.beta2, 1e-3 * (32.0 / w.cells[0]) ** 2)
+        boxes += int(np.prod(w.nsub))
+    assert boxes == 512
