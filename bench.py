@@ -206,7 +206,56 @@ def oracle_sample(iterations: int, budget_rows: int = 15000):
               f"KKT matvec ({t_mv:.2f} s), ILU(0) factor+solve of the leading {rows_f} rows of an interior fine "
               f"subdomain and {rows_c} rows of a coarse one, single-threaded numpy reductions for CGS2; extrapolated to all subdomain "
               f"rows and {iterations} FGMRES iterations; sample wall {time.time() - t_all:.1f} s")
-    return est, sample
+    measured = {"matvec_levelwise_32x32x32x64_s": t_mv, "config1": oracle_config1()}
+    return est, sample, measured
+
+
+def oracle_config1():
+    """The oracle's whole solve of the 8^3 x 16 implicit-Euler workload, timed end to end (measured,
+    not extrapolated): assembly of F_h, one-level RAS 2x2x2x2 with exact local LU (SuperLU), GMRES(30)
+    to 1e-8, on one core."""
+    from oracle import forward, kkt, krylov, schwarz
+    from paper_1508_06103_gb300 import workloads as W
+
+    w = W.tiny(theta=1.0)
+    p = kkt.Problem.from_workload(w)
+    cobs = forward.observations(p, forward.forward_march(p, w.true_source()), w.noise(), w.noise_eps)
+    t0 = time.time()
+    b = kkt.rhs(p, cobs)
+    F = kkt.assemble(p)
+    ras = schwarz.RAS(p, F, w.nsub, w.overlap, "lu")
+    t1 = time.time()
+    sol = krylov.gmres(lambda u: F @ u, b, ras.apply, restart=30, rtol=1e-8, maxit=400)
+    t2 = time.time()
+    return {"workload": "8^3 x 16 implicit Euler, one-level RAS 2x2x2x2 overlap 1, exact local LU, GMRES(30) to 1e-8",
+            "setup_s": t1 - t0, "solve_s": t2 - t1, "total_s": t2 - t0, "iterations": sol.iterations,
+            "true_relres": sol.relres}
+
+
+def gpu_config1(api, W):
+    """The same 8^3 x 16 solve on the GPU (set-up of the exact local LU factors + GMRES to 1e-8)."""
+    import torch
+
+    from oracle import forward, kkt
+
+    w = W.tiny(theta=1.0)
+    p = kkt.Problem.from_workload(w)
+    cobs = torch.from_numpy(forward.observations(p, forward.forward_march(p, w.true_source()), w.noise(),
+                                                 w.noise_eps)).cuda()
+    prob = api.Problem.from_workload(w)
+    out = {}
+    for rep in range(2):   # the first pass loads the kernels
+        torch.cuda.synchronize()
+        t0 = time.time()
+        ras = api.RAS(prob, w.nsub, w.overlap, 64, local="lu")
+        b = prob.rhs(cobs)
+        t1 = time.time()
+        x, st, its, rel = api.gmres_solve(prob, b, ras=ras, restart=30, rtol=1e-8, maxit=400)
+        torch.cuda.synchronize()
+        t2 = time.time()
+        out = {"setup_s": t1 - t0, "solve_s": t2 - t1, "total_s": t2 - t0, "iterations": its, "true_relres": rel}
+        ras.close()
+    return out
 
 
 def reference_arm(args):
@@ -221,8 +270,9 @@ def reference_arm(args):
     for _ in range(args.warmup):
         pass   # the oracle has no warm-up state; warm-up steps are not repeated
     t0 = time.time()
+    measured = {}
     for _ in range(args.steps):
-        v, sample = oracle_sample(ORACLE_ITERATIONS, budget_rows=15000)
+        v, sample, measured = oracle_sample(ORACLE_ITERATIONS, budget_rows=15000)
         vals.append(v)
     wall = time.time() - t0
     value = float(sorted(vals)[len(vals) // 2])
@@ -231,7 +281,9 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(w, {"factor_precision": "fp64 (oracle)"}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "value_is": "extrapolated from the measured parts of the sample",
+                         "host_cores": os.cpu_count(), "measured": measured},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "sample_wall_s": wall,
     }
@@ -437,8 +489,11 @@ def gpu_arm(args):
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
-        est, sample = oracle_sample(int(mixed.get("iters") or ORACLE_ITERATIONS))
-        line["cpu_baseline"] = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        est, sample, measured = oracle_sample(int(mixed.get("iters") or ORACLE_ITERATIONS))
+        line["cpu_baseline"] = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                "value_is": "extrapolated from the measured parts of the sample",
+                                "host_cores": os.cpu_count(), "measured": measured,
+                                "gpu_same_config1": gpu_config1(api, W)}
     print(json.dumps(line))
 
 
@@ -475,7 +530,7 @@ def kernel_arm(args):
 
     build.build()
     c, M = args.cells, args.levels
-    w = W.mid(cells=(c, c, c), M=M, coarse_cells=None, coarse_M=None)
+    w = W.mid(cells=(c, c, c), M=M, coarse_cells=None, coarse_M=None, overlap=args.overlap)
     prob = api.Problem.from_workload(w)
     x = torch.randn(prob.n, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
@@ -490,7 +545,7 @@ def kernel_arm(args):
         print(json.dumps({"kernel": "peaks", **res}))
         return
     if args.kernel == "ras":
-        shape = None if not (args.chunk or args.stages) else (args.chunk, args.stages, 0, 0)
+        shape = None if not (args.chunk or args.stages or args.place) else (args.chunk, args.stages, 0, args.place)
         ras = api.RAS(prob, w.nsub, w.overlap, args.prec, shape=shape)
         ras.apply(x, y)
         torch.cuda.synchronize()
@@ -756,6 +811,54 @@ def batch_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def examples_arm(args):
+    """The paper's Examples 1-3 (Sec. 4.1) at the paper's sizes: one-level space-time RAS with
+    4 x 4 x 4 x 4 subdomains (the paper's np = 256), overlap 1, ILU(0) local solves in FP32 inside
+    FP64 GMRES(30) (the paper's one-level runs use GMRES(50) to 1e-6; here 1e-8), and the
+    two-level form where the steps allow a nested coarse level.  The right-hand sides come from
+    seeded standard normal sensor values (the observation data only enter b; the operator and the
+    preconditioner are the example's), so no forward solve is needed.  One JSON line per case:
+    iterations, solve time (CUDA events) and the set-up time of the factors.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    build.build()
+    cases = [("example1", W.example1()), ("example2-h1h1", W.example2("h1h1")), ("example2-h1l2", W.example2("h1l2")),
+             ("example3-s21", W.example3(21)), ("example3-s9", W.example3(9))]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, w in cases:
+        prob = api.Problem.from_workload(w)
+        rng = np.random.Generator(np.random.PCG64(17))
+        cobs = torch.from_numpy(rng.standard_normal((w.M + 1, len(w.sensor_xyz)))).cuda()
+        b = prob.rhs(cobs)
+        ras = api.RAS(prob, w.nsub, w.overlap, 32)
+        for levels in (1, 2):
+            co = None
+            if levels == 2:
+                # coarse level: half the cells; half the steps when the step count is even, a third
+                # when it divides by 3, else all of them (47 is prime)
+                cM = w.M // 2 if w.M % 2 == 0 else (w.M // 3 if w.M % 3 == 0 else w.M)
+                co = api.Coarse(prob, tuple(c // 2 for c in w.cells), cM, w.nsub, 1, 0.1, 4, 32)
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            e0.record()
+            _, st, its, rel = api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=30, rtol=1e-8, maxit=3000,
+                                              flexible=True)
+            e1.record()
+            torch.cuda.synchronize()
+            print(json.dumps({"case": name, "levels": levels, "cells": list(w.cells), "steps": w.M,
+                              "unknowns": prob.n, "sensors": len(w.sensor_xyz), "status": st, "iterations": its,
+                              "true_relres": rel, "solve_ms": e0.elapsed_time(e1)}), flush=True)
+            if co is not None:
+                co.close()
+        ras.close()
+        prob.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -773,13 +876,16 @@ def main():
     ap.add_argument("--prec", type=int, default=32)
     ap.add_argument("--chunk", type=int, default=0, help="--kernel ras: points per chunk (0: the library's choice)")
     ap.add_argument("--stages", type=int, default=0, help="--kernel ras: copy-ring buffers (0: the library's choice)")
+    ap.add_argument("--place", type=int, default=0,
+                    help="--kernel ras: local vectors 1 in shared, 2 in global memory (0: the library's choice)")
+    ap.add_argument("--overlap", type=int, default=2, help="--kernel ras/matvec: subdomain overlap")
     ap.add_argument("--data", choices=["same-mesh", "refined2"], default="same-mesh",
                     help="observations: same-mesh forward solve (default) or one on a 2x finer mesh")
     ap.add_argument("--maxit", type=int, default=400,
                     help="--workload large: FGMRES iteration limit of a step (the solve converges slowly)")
     ap.add_argument("--coarse-levels", type=int, default=0,
                     help="--workload large: time steps of the coarse level (0: the workload's)")
-    ap.add_argument("--workload", choices=["mid", "large", "batch"], default="mid",
+    ap.add_argument("--workload", choices=["mid", "large", "batch", "examples"], default="mid",
                     help="large: time the 64^3 x 128 single solve; batch: eight independent problems solved "
                          "together; instead of the default benchmark")
     args = ap.parse_args()
@@ -787,6 +893,8 @@ def main():
         large_arm(args)
     elif args.workload == "batch":
         batch_arm(args)
+    elif args.workload == "examples":
+        examples_arm(args)
     elif args.kernel == "sweep":
         sweep_arm(args)
     elif args.kernel:

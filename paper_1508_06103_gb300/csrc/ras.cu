@@ -538,17 +538,13 @@ size_t solve_smem(int cpmax, int nstage, size_t esz, size_t vsz, long long max_p
 
 // Chunk size, copy-ring depth and local-vector placement of the subdomain
 // solve.  Each box is one CTA that steps through its chunks one after the
-// other, so a step's latency decides the time, and most of it is the gathers
-// of neighbour values from the local vector.  The order of preference, as
-// measured on GB300 at 32^3 x 64 (fine boxes) and 16^3 x 32 (coarse-sized
-// boxes), FP32 and FP64: the local vector in shared memory when it fits; the
-// fewest waves of CTAs over the SMs (the runtime's occupancy for the shared
-// memory, threads and registers); the shallowest ring (a deeper ring takes
-// shared memory from the L1 that caches a global local vector, and lost
-// 30-45 % in every case measured); in FP32, 8 lanes per point when the
-// vector is in shared memory (0.28 vs 0.45 ms on the coarse-sized boxes) and
-// 4 when it is in global memory (3.95 vs 4.37 ms at 32^3 x 64); the largest
-// chunk (fewest steps).
+// other, so a step's latency decides the time.  The order of preference, as
+// measured on GB300 (32^3 x 64 fine boxes, coarse-sized boxes, FP32 and
+// FP64): the fewest waves of CTAs over the SMs (the runtime's occupancy for
+// the shared memory, threads and registers); the local vectors in global
+// memory (cached in L1) rather than in shared memory; the shallowest ring (a
+// deeper ring takes shared memory from the L1 that caches the local
+// vectors); the largest chunk (fewest steps).  ras_autotune measures instead.
 struct SolveShape {
   int ch, cpmax, nstage, lanes;
   bool smem_vec;
@@ -590,8 +586,11 @@ kkt_status choose_solve_shape(int nbox, long long max_pad, int nsm, const ShapeR
             &per_sm, sv ? solve_kernel<T, true>() : solve_kernel<T, false>(), threads, sm));
         if (per_sm < 1) continue;
         const long long waves = (nbox + (long long)nsm * per_sm - 1) / ((long long)nsm * per_sm);
-        // smaller key is better
-        const long long key = (sv ? 0 : 1000000000LL) + waves * 100000 + (ns - 2) * 1000 + (100 - ch);
+        // smaller key is better: fewest waves, then the local vectors in global
+        // memory (measured faster than in shared memory with this kernel, also on
+        // the small coarse-level boxes: 0.285 vs 0.354 ms at 17^3 x 33 nodes, 4^4
+        // boxes, overlap 1), the shallowest ring, the largest chunk
+        const long long key = waves * 100000000LL + (sv ? 1000000 : 0) + (ns - 2) * 1000 + (100 - ch);
         if (best_key < 0 || key < best_key) {
           best_key = key;
           best = SolveShape{ch, cp, ns, kLanes, sv != 0};
