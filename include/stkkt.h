@@ -164,7 +164,7 @@ kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, 
  *   decides how the solve kernel runs, not what it computes: every compiled
  *   shape applies the same ILU(0) factors.
  *   shape[0]  points per chunk of a wavefront (FP64: 34, 26, 18; FP32: 52, 36,
- *             20; BF16: 104, 72, 40)
+ *             20; BF16: 72, 40, 8)
  *   shape[1]  buffers of the factor-copy ring, 2..4
  *   shape[2]  lanes per point: 4 (the one compiled)
  *   shape[3]  1 = local vectors in shared memory, 2 = in global memory

@@ -57,15 +57,25 @@ __device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
 // ahead of their use; halo nodes outside the domain are zero-filled, so the
 // passes need no bounds tests.
 // ---------------------------------------------------------------------------
-constexpr int TX = 8, TY = 8, TZ = 4, NT = 16;
-constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, NH = HX * HY * HZ;
-constexpr int NXP = TX * HY * HZ;   // x-pass outputs: tile in x, halo in y and z
-constexpr int NYP = TX * TY * HZ;   // y-pass outputs: tile in x and y, halo in z
-constexpr int kMvThreads = TX * TY * TZ;
+// Tile shapes (nodes per CTA along x, y, z): 8 x 8 x 4, or 11 x 11 x 2, which
+// covers grids of 11 k nodes per axis without ragged tiles (33^3 and 65^3
+// nodes: 40 x 40 x 36 / 33^3 = 1.6x the nodes with 8 x 8 x 4 tiles); the host
+// picks the shape with the least estimated work (launch_tiled).
+constexpr int NT = 16;   // levels per CTA
+template <int TX_, int TY_, int TZ_>
+struct Tile {
+  static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
+  static constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, NH = HX * HY * HZ;
+  static constexpr int NXP = TX * HY * HZ;   // x-pass outputs: tile in x, halo in y and z
+  static constexpr int NYP = TX * TY * HZ;   // y-pass outputs: tile in x and y, halo in z
+  static constexpr int kThreads = TX * TY * TZ;
+};
+using TileA = Tile<8, 8, 4>;
+using TileB = Tile<11, 11, 2>;
 
-template <typename T>
+template <typename T, typename Tl>
 constexpr size_t mv_smem() {
-  return sizeof(T) * (4 * 3 * NH + 6 * NH + 5 * NXP + 5 * NYP);
+  return sizeof(T) * (4 * 3 * Tl::NH + 6 * Tl::NH + 5 * Tl::NXP + 5 * Tl::NYP);
 }
 
 // 1D linear-element mass and stiffness rows on one axis of n nodes with
@@ -152,11 +162,13 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // kL2: the H1-L2 regularisation (its beta2 term goes through B), a template
 // argument so the H1-H1 kernel carries no test for it.
-template <typename T, bool kL2>
-__global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T* __restrict__ x,
-                                                           T* __restrict__ y, const double* __restrict__ b,
-                                                           int tiles_x, int tiles_y, Axis1D<T> ax, Axis1D<T> ay,
-                                                           Axis1D<T> az, LevelW<T> W) {
+template <typename T, bool kL2, typename Tl>
+__global__ void __launch_bounds__(Tl::kThreads) matvec_tiled(DevProblem p, const T* __restrict__ x,
+                                                             T* __restrict__ y, const double* __restrict__ b,
+                                                             int tiles_x, int tiles_y, Axis1D<T> ax, Axis1D<T> ay,
+                                                             Axis1D<T> az, LevelW<T> W) {
+  constexpr int TX = Tl::TX, TY = Tl::TY, TZ = Tl::TZ;
+  constexpr int HX = Tl::HX, HY = Tl::HY, NH = Tl::NH, NXP = Tl::NXP, NYP = Tl::NYP;
   if (gated_off(p.gate)) return;
   extern __shared__ __align__(16) unsigned char mv_sm[];
   T* Xs = reinterpret_cast<T*>(mv_sm);   // [4 slots][3 components][NH]
@@ -307,9 +319,19 @@ __global__ void __launch_bounds__(kMvThreads) matvec_tiled(DevProblem p, const T
   cp_async_wait<0>();
 }
 
-template <typename T>
-void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
-  const int tx = (p.nx + TX - 1) / TX, ty = (p.ny + TY - 1) / TY, tz = (p.nz + TZ - 1) / TZ;
+// Estimated multiply-adds of one level over the grid with tile shape Tl: the
+// six time combinations on every halo node, the x and y passes, and the z pass
+// with the two 27-point stencils per tile node (ragged tiles count in full).
+template <typename Tl>
+double tile_work(const DevProblem& p) {
+  const double tiles = (double)((p.nx + Tl::TX - 1) / Tl::TX) * ((p.ny + Tl::TY - 1) / Tl::TY) *
+                       ((p.nz + Tl::TZ - 1) / Tl::TZ);
+  return tiles * (25.0 * Tl::NH + 30.0 * Tl::NXP + 36.0 * Tl::NYP + 138.0 * Tl::kThreads);
+}
+
+template <typename T, typename Tl>
+void launch_shape(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
+  const int tx = (p.nx + Tl::TX - 1) / Tl::TX, ty = (p.ny + Tl::TY - 1) / Tl::TY, tz = (p.nz + Tl::TZ - 1) / Tl::TZ;
   dim3 grid(tx * ty * tz, (p.M + 1 + NT - 1) / NT);
   Axis1D<T> ax, ay, az;
   ax.init(p.nx, p.hx);
@@ -319,9 +341,15 @@ void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaSt
   w.init(p.tau, p.theta, p.beta1, p.beta2);
   // (the dynamic shared-memory limits are raised once, in matvec_prepare)
   if (p.reg != 0)
-    matvec_tiled<T, true><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+    matvec_tiled<T, true, Tl><<<grid, Tl::kThreads, mv_smem<T, Tl>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
   else
-    matvec_tiled<T, false><<<grid, kMvThreads, mv_smem<T>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+    matvec_tiled<T, false, Tl><<<grid, Tl::kThreads, mv_smem<T, Tl>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+}
+
+template <typename T>
+void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
+  if (tile_work<TileB>(p) < tile_work<TileA>(p)) launch_shape<T, TileB>(p, x, y, b, s);
+  else launch_shape<T, TileA>(p, x, y, b, s);
 }
 
 __global__ void d2f(const double* __restrict__ x, float* __restrict__ y, long long n, const int* gate) {
@@ -345,15 +373,20 @@ __global__ void sub_f2d(const double* __restrict__ b, const float* __restrict__ 
 
 }  // namespace
 
+template <typename T, typename Tl>
+kkt_status prepare_shape() {
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<T, false, Tl>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mv_smem<T, Tl>()));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<T, true, Tl>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mv_smem<T, Tl>()));
+  return KKT_OK;
+}
+
 kkt_status matvec_prepare() {
-  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mv_smem<double>()));
-  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mv_smem<double>()));
-  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mv_smem<float>()));
-  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mv_smem<float>()));
+  KKT_TRY((prepare_shape<double, TileA>()));
+  KKT_TRY((prepare_shape<double, TileB>()));
+  KKT_TRY((prepare_shape<float, TileA>()));
+  KKT_TRY((prepare_shape<float, TileB>()));
   return KKT_OK;
 }
 

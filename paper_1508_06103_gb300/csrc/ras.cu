@@ -156,7 +156,7 @@ struct ChunkCfg<double> {
 };
 template <>
 struct ChunkCfg<__nv_bfloat16> {                      // FP32 factors stored as BF16
-  static constexpr int CH = 104, CH2 = 72, CH3 = 40;
+  static constexpr int CH = 72, CH2 = 40, CH3 = 8;
   static constexpr int Q = 32, R = 8;                  // cp = 8 (mod 32): two values per bank word
 };
 constexpr int kLanes = 4;   // lanes per point of the subdomain solve
@@ -183,6 +183,16 @@ int chunk_stride(int n) {
   const int Q = ChunkCfg<S>::Q, R = ChunkCfg<S>::R;
   return n <= R ? R : R + ((n - R + Q - 1) / Q) * Q;
 }
+template <typename S>
+__host__ __device__ constexpr int chunk_stride_dev(int n) {
+  return n <= ChunkCfg<S>::R ? ChunkCfg<S>::R
+                             : ChunkCfg<S>::R + ((n - ChunkCfg<S>::R + ChunkCfg<S>::Q - 1) / ChunkCfg<S>::Q) *
+                                                    ChunkCfg<S>::Q;
+}
+static_assert(chunk_stride_dev<float>(ChunkCfg<float>::CH) == ChunkCfg<float>::CH, "full FP32 chunk unpadded");
+static_assert(chunk_stride_dev<double>(ChunkCfg<double>::CH) == ChunkCfg<double>::CH, "full FP64 chunk unpadded");
+static_assert(chunk_stride_dev<__nv_bfloat16>(ChunkCfg<__nv_bfloat16>::CH) == ChunkCfg<__nv_bfloat16>::CH,
+              "full BF16 chunk unpadded");
 int chunk_stride_of(int prec, int n) {
   if (prec == 64) return chunk_stride<double>(n);
   if (prec == 16) return chunk_stride<__nv_bfloat16>(n);
@@ -409,8 +419,12 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
     vq_cur = j < cur.n ? vtab[bx.poff + cur.q0 + j] : 0;
   }
   // one step of either sweep; false when a copy wait gave up (the CTA stops)
-  auto step = [&](int g, auto upper_tag) -> bool {
+  // kCp: the row stride of the chunk's block as a compile-time constant (a
+  // full chunk: kCp = CH, so every factor read is [base + immediate]), or 0 for
+  // the run-time stride of a ragged chunk
+  auto step = [&](int g, auto upper_tag, auto cp_tag) -> bool {
     constexpr bool kUpper = decltype(upper_tag)::value;
+    constexpr int kCp = decltype(cp_tag)::value;
     const int b = g % nstage;
     if (threadIdx.x == 0 && g + nstage - 1 < nblk) {
       issue(iss, g + nstage - 1);
@@ -420,7 +434,7 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
     const int vq_nxt = (g + 1 < nblk && j < nxt.n) ? vtab[bx.poff + nxt.q0 + j] : 0;
     const Chunk& c = cur;
     const bool act = j < c.n;
-    const int cp = c.cp;
+    const int cp = kCp ? kCp : c.cp;
     T* vp = v + (act ? vq_cur : 0);
     // all neighbour loads of the step first (they depend on the previous steps
     // only, so they are in flight while the factor block is awaited), then the
@@ -493,8 +507,15 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
   };
   // forward sweep (unit lower factor), then backward sweep (upper factor)
   bool ok = true;
-  for (int g = 0; ok && g < nch; ++g) ok = step(g, std::false_type{});
-  for (int g = nch; ok && g < nblk; ++g) ok = step(g, std::true_type{});
+  using FullCp = std::integral_constant<int, ChunkCfg<S>::CH>;   // == chunk_stride(CH): no padding
+  using AnyCp = std::integral_constant<int, 0>;
+  const int full_cp = chunk_stride_dev<S>(ChunkCfg<S>::CH);
+  for (int g = 0; ok && g < nch; ++g)
+    ok = cur.cp == full_cp && full_cp == FullCp::value ? step(g, std::false_type{}, FullCp{})
+                                                       : step(g, std::false_type{}, AnyCp{});
+  for (int g = nch; ok && g < nblk; ++g)
+    ok = cur.cp == full_cp && full_cp == FullCp::value ? step(g, std::true_type{}, FullCp{})
+                                                       : step(g, std::true_type{}, AnyCp{});
   if (!ok) {
     // A wait gave up at block gf (status 2 is set): the blocks gf .. gf +
     // nstage - 1 may still be in flight into this CTA's buffers.  Thread 0
