@@ -1,21 +1,28 @@
-"""Q1 (trilinear) finite elements on a uniform box and the 1D time elements.
+"""Spatial finite elements on a uniform box, and the 1D time elements.
 
 Test infrastructure (see the package header).
 
 The paper discretises the state and adjoint equations with continuous
-piecewise-linear elements in space (Sec. 3.1, Eq. 8) and the source with
-piecewise-linear elements in space and time (Eq. 9).  On the structured
-hexahedral grid used here the spatial elements are trilinear (Q1).  The
-Appendix names the matrices:
+piecewise-linear elements in space on a regular triangulation (Sec. 3.1,
+Eq. 8) and the source with piecewise-linear elements in space and time
+(Eq. 9).  Two spatial elements are built on the structured grid of cells:
+  "q1": trilinear elements on the hexahedral cells;
+  "p1": piecewise-linear elements on the Kuhn split of every cell into six
+        tetrahedra around its main diagonal (0,0,0)-(1,1,1) (the same split
+        in every cell, so the triangulation is conforming).
+The Appendix names the matrices:
 
     A = (a grad phi_i, grad phi_j)          stiffness with diffusivity a
     B = (phi_i, phi_j)                      mass
     E : convection, (div(v phi), phi)       state and adjoint use E and E^T
     L^{mn}, K^{mn}, D^{mn}                  space-time blocks of the f equation
 
-Every element matrix is obtained by integrating the basis functions with
+Every Q1 element matrix is obtained by integrating the basis functions with
 2-point Gauss quadrature per axis, which is exact for these integrands
-(degree <= 2 per axis).  Coefficients a and v are constant per cell.
+(degree <= 2 per axis).  A P1 cell matrix is the sum over its six
+tetrahedra; on each, the barycentric coordinates come from inverting the
+4x4 vertex matrix and the integrals from the symmetric 4-point rule, exact
+for degree 2.  Coefficients a and v are constant per cell.
 
 Convention for E (the reading of the weak form Eq. 8): the state row i
 (test function phi_i) and column j (trial phi_j) hold
@@ -23,11 +30,14 @@ Convention for E (the reading of the weak form Eq. 8): the state row i
 and the adjoint operator uses its exact transpose.
 
 Pins: tests/test_oracle_fem.py (Kronecker closed forms, row sums, total
-mass, transpose identity).
+mass, transpose identity; for P1: the mass row sums k V / 24 of a node in k
+tetrahedra, exact integrals of products of linear functions for B, K and E,
+the 15-point coupling of the split, the 7-point Laplacian stencil).
 """
 
 from __future__ import annotations
 
+import itertools
 import math
 
 import numpy as np
@@ -81,6 +91,57 @@ def element_matrices(hx: float, hy: float, hz: float):
     return Me, Ke, G
 
 
+def kuhn_tetrahedra():
+    """Local node ids (l = lx + 2 ly + 4 lz) of the six tetrahedra of the Kuhn split.
+
+    For each ordering (i, j, k) of the axes the tetrahedron runs from node 0
+    along e_i, then e_j, then e_k to node 7: the points with
+    1 >= s_i >= s_j >= s_k >= 0 in cell coordinates s = x / h.
+    """
+    out = []
+    for i, j, _ in itertools.permutations(range(3)):
+        a = 1 << i
+        out.append((0, a, a | (1 << j), 7))
+    return out
+
+
+# symmetric 4-point rule on a tetrahedron, exact for degree 2 (barycentric
+# point (A, B, B, B) and its permutations, weight |T| / 4 each)
+_TQ_A = (5.0 + 3.0 * math.sqrt(5.0)) / 20.0
+_TQ_B = (5.0 - math.sqrt(5.0)) / 20.0
+
+
+def element_matrices_p1(hx: float, hy: float, hz: float):
+    """8x8 cell matrices (Me, Ke, G) of P1 elements on the Kuhn split of one cell.
+
+    Same layout and meaning as element_matrices; each is the sum of the
+    4x4 tetrahedron matrices scattered to the cell's local nodes.
+    """
+    h = np.array([hx, hy, hz])
+    Me = np.zeros((8, 8))
+    Ke = np.zeros((8, 8))
+    G = np.zeros((3, 8, 8))
+    for tet in kuhn_tetrahedra():
+        X = np.array([[(l & 1) * h[0], ((l >> 1) & 1) * h[1], ((l >> 2) & 1) * h[2]] for l in tet])
+        Tm = np.vstack([np.ones(4), X.T])   # columns (1, x, y, z) of the vertices
+        vol = abs(np.linalg.det(Tm)) / 6.0
+        inv = np.linalg.inv(Tm)             # lambda_k(x) = inv[k] . (1, x, y, z)
+        grad = inv[:, 1:]                   # (4, 3): grad lambda_k
+        idx = list(tet)
+        for q in range(4):
+            lam = np.full(4, _TQ_B)
+            lam[q] = _TQ_A
+            w = vol / 4.0
+            Me[np.ix_(idx, idx)] += w * np.outer(lam, lam)
+            Ke[np.ix_(idx, idx)] += w * grad @ grad.T
+            for d in range(3):
+                G[d][np.ix_(idx, idx)] += w * np.outer(lam, grad[:, d])
+    return Me, Ke, G
+
+
+ELEMENTS = ("q1", "p1")
+
+
 def cell_nodes(cells) -> np.ndarray:
     """(ncell, 8) global node ids of each cell's local nodes."""
     cx, cy, cz = cells
@@ -106,13 +167,16 @@ def _assemble(cells, coef_elem) -> sp.csr_matrix:
     return sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
 
 
-def spatial_matrices(cells, lengths, a_cell, v_cell):
+def spatial_matrices(cells, lengths, a_cell, v_cell, element: str = "q1"):
     """Global B (mass), A (stiffness with a), E_s (state convection), K (Laplacian).
 
     Appendix element matrices; E_s follows the weak form of Eq. 8 (row = test).
+    element: "q1" (trilinear hexahedra) or "p1" (linear tetrahedra, Kuhn split).
     """
+    if element not in ELEMENTS:
+        raise ValueError(f"element must be one of {ELEMENTS}")
     hx, hy, hz = (l / c for l, c in zip(lengths, cells))
-    Me, Ke, G = element_matrices(hx, hy, hz)
+    Me, Ke, G = (element_matrices if element == "q1" else element_matrices_p1)(hx, hy, hz)
     ncell = int(np.prod(cells))
     a_cell = np.asarray(a_cell, dtype=np.float64).reshape(ncell)
     v_cell = np.asarray(v_cell, dtype=np.float64).reshape(ncell, 3)

@@ -28,6 +28,10 @@ K is the stiffness matrix of the H1-H1 regularisation N_beta (Eq. 3, the
 (Example 2) replaces |grad f|^2 by f^2, so K becomes the mass matrix B
 there (reg = "h1l2").
 
+The spatial matrices B, A, E_s and K come from oracle.fem with either Q1
+elements on the hexahedral cells (element = "q1") or P1 elements on the
+Kuhn split of every cell (element = "p1"); the block rows are the same.
+
 B3 = diag(s), s_j = number of sensors snapped to node j.  On Dirichlet nodes
 (Gamma_1) the C and G rows are identity rows (the columns are kept), with
 right-hand side p = 0 (all workloads use homogeneous Dirichlet data); the
@@ -53,7 +57,7 @@ class Problem:
     """Discrete data of one inverse problem (everything the KKT needs)."""
 
     def __init__(self, cells, lengths, T, M, theta, dirichlet_faces, a_cell, v_cell,
-                 sensor_node, beta1, beta2, reg="h1h1"):
+                 sensor_node, beta1, beta2, reg="h1h1", element="q1"):
         self.cells = tuple(int(c) for c in cells)
         self.lengths = tuple(float(l) for l in lengths)
         self.nodes = tuple(c + 1 for c in self.cells)
@@ -72,7 +76,9 @@ class Problem:
         if reg not in ("h1h1", "h1l2"):
             raise ValueError("reg must be 'h1h1' or 'h1l2'")
         self.reg = reg
-        self.B, self.A, self.Es, self.K = fem.spatial_matrices(self.cells, self.lengths, self.a_cell, self.v_cell)
+        self.element = element
+        self.B, self.A, self.Es, self.K = fem.spatial_matrices(self.cells, self.lengths, self.a_cell, self.v_cell,
+                                                               element)
         # spatial matrix of the beta2 term: stiffness (H1-H1) or mass (H1-L2)
         self.W2 = self.K if reg == "h1h1" else self.B
         self.S = (self.A + self.Es).tocsr()
@@ -87,7 +93,8 @@ class Problem:
     @classmethod
     def from_workload(cls, w):
         return cls(w.cells, w.lengths, w.T, w.M, w.theta, w.dirichlet_faces, w.a_cell,
-                   w.v_cell, w.sensor_nodes(), w.beta1, w.beta2, getattr(w, "reg", "h1h1"))
+                   w.v_cell, w.sensor_nodes(), w.beta1, w.beta2, getattr(w, "reg", "h1h1"),
+                   getattr(w, "element", "q1"))
 
     # index helpers ------------------------------------------------------
     def pb_index(self, n, j, c):

@@ -333,7 +333,8 @@ def coarse_problem(pf: kkt.Problem, ccells: Sequence[int], cM: int) -> kkt.Probl
     cxn = ccells[0] + 1
     cyn = ccells[1] + 1
     sc = snap(ix, rx) + cxn * (snap(iy, ry) + cyn * snap(iz, rz))
-    return kkt.Problem(ccells, pf.lengths, pf.T, cM, pf.theta, pf.faces, ac, vc, sc, pf.beta1, pf.beta2, pf.reg)
+    return kkt.Problem(ccells, pf.lengths, pf.T, cM, pf.theta, pf.faces, ac, vc, sc, pf.beta1, pf.beta2, pf.reg,
+                       pf.element)
 
 
 class TwoLevel:

@@ -78,6 +78,8 @@ class Workload:
     rtol: float = 1e-8
     # regularisation: "h1h1" (N_beta, Eq. 3) or "h1l2" (beta2 |grad f|^2 -> beta2 f^2, Sec. 4 Example 2)
     reg: str = "h1h1"
+    # spatial element: "q1" (trilinear hexahedra) or "p1" (linear tetrahedra, Kuhn split of each cell)
+    element: str = "q1"
 
     # ---- derived sizes -------------------------------------------------
     @property

@@ -1,5 +1,7 @@
 """Pins of the oracle's Schwarz preconditioners and Krylov solvers (Sec. 3.2, 4)."""
 
+import dataclasses
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -8,9 +10,9 @@ from oracle import kkt, krylov, schwarz
 from paper_1508_06103_gb300 import workloads as W
 
 
-def _small(seed=21, cells=(3, 3, 2), M=3, faces=W.FACE_X0):
+def _small(seed=21, cells=(3, 3, 2), M=3, faces=W.FACE_X0, element="q1"):
     w = W.random_small(seed, cells=cells, M=M, dirichlet_faces=faces, nsens=4)
-    p = kkt.Problem.from_workload(w)
+    p = kkt.Problem.from_workload(dataclasses.replace(w, element=element))
     return p, kkt.assemble(p)
 
 
@@ -30,9 +32,13 @@ def test_owned_sets_partition_the_unknowns():
     assert np.all(owner == 1)
 
 
-def test_ilu0_defining_property_on_pattern():
-    """(L U)_ij = a_ij for every (i, j) in the pattern (the definition of ILU(0))."""
-    p, F = _small()
+@pytest.mark.parametrize("element", ["q1", "p1"])
+def test_ilu0_defining_property_on_pattern(element):
+    """(L U)_ij = a_ij for every (i, j) in the pattern (the definition of ILU(0)).
+
+    For P1 the structural pattern is still the 27-point cell-sharing stencil:
+    the entries the Kuhn split does not couple are structural zeros."""
+    p, F = _small(element=element)
     b = schwarz.boxes(p, (2, 1, 1, 2), 1)[1]
     idx, _ = schwarz.box_unknowns(p, b)
     Aloc = F[idx][:, idx].toarray()
@@ -152,6 +158,9 @@ def test_coarse_problem_averages_and_resnaps():
     wf = W.random_small(2, cells=(4, 4, 2), M=4, nsens=5)
     pf = kkt.Problem.from_workload(wf)
     pc = schwarz.coarse_problem(pf, (2, 2, 1), 2)
+    assert pc.element == "q1"
+    assert schwarz.coarse_problem(kkt.Problem.from_workload(dataclasses.replace(wf, element="p1")),
+                                  (2, 2, 1), 2).element == "p1"
     a = pf.a_cell.reshape(2, 4, 4)
     assert np.isclose(pc.a_cell[0], a[0:2, 0:2, 0:2].mean())
     assert np.isclose(pc.a_cell.mean(), pf.a_cell.mean())
@@ -159,8 +168,9 @@ def test_coarse_problem_averages_and_resnaps():
     assert pc.s.sum() == pf.s.sum()
 
 
-def test_two_level_with_identical_coarse_mesh_and_exact_coarse_solve_is_exact():
-    p, F = _small(cells=(2, 2, 2), M=2, faces=W.FACE_X0)
+@pytest.mark.parametrize("element", ["q1", "p1"])
+def test_two_level_with_identical_coarse_mesh_and_exact_coarse_solve_is_exact(element):
+    p, F = _small(cells=(2, 2, 2), M=2, faces=W.FACE_X0, element=element)
     tl = schwarz.TwoLevel(p, F, (2, 1, 1, 1), 1, p.cells, p.M, c_overlap=0, c_rtol=1e-14,
                           c_maxit=200, local="ilu0")
     tl.coarse = schwarz.RAS(tl.pc, tl.Fc, (1, 1, 1, 1), 0, "lu")
