@@ -56,6 +56,10 @@ typedef int kkt_status;
 #define KKT_FACE_Z0 16u
 #define KKT_FACE_Z1 32u
 
+/* Spatial elements on the grid's cells (Sec. 3.1; kkt_set_element). */
+#define KKT_ELEM_Q1 0   /* trilinear elements on the hexahedral cells (the default) */
+#define KKT_ELEM_P1 1   /* linear elements on the Kuhn split of every cell into six tetrahedra */
+
 /* Uniform grid of cx*cy*cz hexahedral cells on [0,lx]x[0,ly]x[0,lz]. */
 typedef struct {
   int cx, cy, cz;
@@ -105,6 +109,27 @@ kkt_status kkt_create(const kkt_grid* g, int nt, double dt, const double* a_cell
  * Host only, no device work.  Errors: ARG (null problem, reg not 0 or 1).
  */
 kkt_status kkt_set_regularization(kkt_problem* p, int reg);
+
+/*
+ * kkt_set_element -- choose the spatial element of B, A, E_s and K (Sec. 3.1:
+ * continuous piecewise-linear elements on a regular triangulation).
+ *   elem KKT_ELEM_Q1: trilinear elements on the hexahedral cells (the default
+ *        after kkt_create; 27-point stencils);
+ *   elem KKT_ELEM_P1: linear elements on the Kuhn split of every cell into six
+ *        tetrahedra around its main diagonal (0,0,0)-(1,1,1), the same split in
+ *        every cell (a conforming triangulation); each node couples with the 14
+ *        neighbours whose offset has all nonzero components of one sign.
+ * The block rows of F_h (Appendix) are the same for both.  The subdomain
+ * factorisations keep the 27-point structural pattern of the grid: under P1
+ * the 12 couplings the split does not make are structural zeros, and ILU(0)
+ * admits fill there.  Reassembles the coefficients from the a and v given to
+ * kkt_create (synchronous, on the legacy default stream); set it before
+ * creating the preconditioners of this problem, as with
+ * kkt_set_regularization; coarse_setup copies the fine level's element.
+ * Errors: ARG (null problem, unknown elem), NOMEM, CUDA (the problem then
+ * keeps its previous element).
+ */
+kkt_status kkt_set_element(kkt_problem* p, int elem);
 
 /* Sizes of a problem: nodes per axis, N, levels M+1 and unknowns 3*N*(M+1). */
 kkt_status kkt_sizes(const kkt_problem* p, int* nx, int* ny, int* nz, int* levels,

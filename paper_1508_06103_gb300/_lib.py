@@ -34,6 +34,7 @@ SIGNATURES = {
                             C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "kkt_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "kkt_set_regularization": (C.c_int, [C.c_void_p, C.c_int]),
+    "kkt_set_element": (C.c_int, [C.c_void_p, C.c_int]),
     "kkt_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "kkt_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ras_setup": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),

@@ -64,11 +64,17 @@ class Problem:
                 w.theta, w.dirichlet_faces)
         if getattr(w, "reg", "h1h1") != "h1h1":
             p.set_regularization(w.reg)
+        if getattr(w, "element", "q1") != "q1":
+            p.set_element(w.element)
         return p
 
     def set_regularization(self, reg: str) -> None:
         """'h1h1' (N_beta, Eq. 3) or 'h1l2' (Sec. 4, Example 2); before building preconditioners."""
         check(self._lib.kkt_set_regularization(self.h, {"h1h1": 0, "h1l2": 1}[reg]), "kkt_set_regularization")
+
+    def set_element(self, element: str) -> None:
+        """'q1' (trilinear hexahedra) or 'p1' (Kuhn split into tetrahedra); before building preconditioners."""
+        check(self._lib.kkt_set_element(self.h, {"q1": 0, "p1": 1}[element]), "kkt_set_element")
 
     def close(self):
         if self.h is not None and self.h.value:

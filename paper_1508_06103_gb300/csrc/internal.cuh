@@ -89,7 +89,8 @@ struct DevProblem {
   long long P;                              // points N * (M+1)
   double tau, theta, beta1, beta2;
   int reg;                                  // beta2 term: 0 stiffness K (H1-H1), 1 mass B (H1-L2)
-  double hx, hy, hz;                        // mesh widths (B and K are tensor products of 1D factors)
+  int elem;                                 // KKT_ELEM_Q1 or KKT_ELEM_P1 (kkt_set_element)
+  double hx, hy, hz;                        // mesh widths (Q1: B and K are tensor products of 1D factors)
   const double *S, *ST, *B, *K;             // [27][N] row coefficients (FP64)
   const float *S32, *ST32, *B32, *K32;      // FP32 copies
   const unsigned char* dir;                 // [N] 1 on Dirichlet nodes
@@ -168,7 +169,8 @@ struct kkt_problem {
   long long P, n;                           // points, unknowns
   double hx, hy, hz, tau, T, theta, beta1, beta2;
   int reg = 0;                              // kkt_set_regularization
-  // host copies used by the coarse level
+  int elem = 0;                             // kkt_set_element
+  // host copies used by the coarse level and by kkt_set_element
   std::vector<double> a_cell, v_cell;
   std::vector<int> sensor_node;
   // device memory

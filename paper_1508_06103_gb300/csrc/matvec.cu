@@ -13,7 +13,9 @@
 //
 // matvec_tiled below computes all three output slots of a space-time point
 // in one pass: four spatial operators applied to six time combinations, B and
-// K by sum factorisation, S and S^T as 27-point stencils.
+// K by sum factorisation, S and S^T as 27-point stencils.  Under P1 elements
+// on the Kuhn split (kkt_set_element) B and K are no tensor products: all four
+// operators are applied as stencils over the 15 offsets the split couples.
 
 #include "internal.cuh"
 
@@ -73,9 +75,17 @@ struct Tile {
 using TileA = Tile<8, 8, 4>;
 using TileB = Tile<11, 11, 2>;
 
-template <typename T, typename Tl>
+template <typename T, typename Tl, bool kP1 = false>
 constexpr size_t mv_smem() {
-  return sizeof(T) * (4 * 3 * Tl::NH + 6 * Tl::NH + 5 * Tl::NXP + 5 * Tl::NYP);
+  return kP1 ? sizeof(T) * (4 * 3 * Tl::NH + 6 * Tl::NH)
+             : sizeof(T) * (4 * 3 * Tl::NH + 6 * Tl::NH + 5 * Tl::NXP + 5 * Tl::NYP);
+}
+
+// Stencil offset d = (dx+1) + 3 (dy+1) + 9 (dz+1) is an edge of the Kuhn split
+// (or the node itself) when its nonzero components all have one sign.
+__host__ __device__ constexpr bool kuhn_offset(int d) {
+  const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+  return !((dx > 0 || dy > 0 || dz > 0) && (dx < 0 || dy < 0 || dz < 0));
 }
 
 // 1D linear-element mass and stiffness rows on one axis of n nodes with
@@ -161,8 +171,9 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // kL2: the H1-L2 regularisation (its beta2 term goes through B), a template
-// argument so the H1-H1 kernel carries no test for it.
-template <typename T, bool kL2, typename Tl>
+// argument so the H1-H1 kernel carries no test for it.  kP1: P1 elements, B and
+// K as stored 15-point stencils (no x and y passes, two barriers per level).
+template <typename T, bool kL2, typename Tl, bool kP1 = false>
 __global__ void __launch_bounds__(Tl::kThreads) matvec_tiled(DevProblem p, const T* __restrict__ x,
                                                              T* __restrict__ y, const double* __restrict__ b,
                                                              int tiles_x, int tiles_y, Axis1D<T> ax, Axis1D<T> ay,
@@ -200,13 +211,19 @@ __global__ void __launch_bounds__(Tl::kThreads) matvec_tiled(DevProblem p, const
       cp_async_value(dst + 2 * NH + h, src + (valid ? 2 : 0), valid);
     }
   };
-  // S and S^T of the thread's node: registers in FP32, reloaded per level in FP64
-  T cS[kStencil], cST[kStencil];
+  // S and S^T (and under P1, B and K) of the thread's node: registers in
+  // FP32, reloaded per level in FP64
+  T cS[kStencil], cST[kStencil], cB[kStencil], cK[kStencil];
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int d = 0; d < kStencil; ++d) {
+      if (kP1 && !kuhn_offset(d)) continue;
       cS[d] = own ? c.S[(size_t)d * N + j] : (T)0;
       cST[d] = own ? c.ST[(size_t)d * N + j] : (T)0;
+      if constexpr (kP1) {
+        cB[d] = own ? c.B[(size_t)d * N + j] : (T)0;
+        cK[d] = own ? c.K[(size_t)d * N + j] : (T)0;
+      }
     }
   }
   prefetch(n0 - 1);
@@ -247,6 +264,49 @@ __global__ void __launch_bounds__(Tl::kThreads) matvec_tiled(DevProblem p, const
     __syncthreads();
     if (n + 3 <= n1) prefetch(n + 3);    // into the slot of level n - 1, no longer read
     cp_async_commit();
+    if constexpr (kP1) {
+      if (own) {
+        T yc = (T)0, yg = (T)0, yf = (T)0;
+#pragma unroll
+        for (int d = 0; d < kStencil; ++d) {
+          if (!kuhn_offset(d)) continue;
+          const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+          const int h = hc + dx + HX * (dy + HY * dz);
+          T s_, st_, b_, k_;
+          if constexpr (sizeof(T) == 4) {
+            s_ = cS[d];
+            st_ = cST[d];
+            b_ = cB[d];
+            k_ = cK[d];
+          } else {
+            s_ = c.S[(size_t)d * N + j];
+            st_ = c.ST[(size_t)d * N + j];
+            b_ = c.B[(size_t)d * N + j];
+            k_ = kL2 ? (T)0 : c.K[(size_t)d * N + j];
+          }
+          yc += b_ * U[h] + s_ * U[NH + h];
+          yg += b_ * U[2 * NH + h] + st_ * U[3 * NH + h];
+          yf += b_ * U[4 * NH + h];
+          if constexpr (!kL2) yf += k_ * U[5 * NH + h];
+        }
+        const bool dirj = p.dir[j] != 0;
+        const T C0 = X0[hc], G0 = X0[NH + hc], Cp = Xp[hc];
+        if (n == 0 || dirj) yc = C0;
+        if (n == M || dirj) yg = G0;
+        else yg += tau * (T)p.sens[j] * (th * Cp + th1 * C0);
+        const long long o = 3 * ((long long)n * N + j);
+        if (b != nullptr) {
+          y[o] = (T)(b[o] - (double)yc);
+          y[o + 1] = (T)(b[o + 1] - (double)yg);
+          y[o + 2] = (T)(b[o + 2] - (double)yf);
+        } else {
+          y[o] = yc;
+          y[o + 1] = yg;
+          y[o + 2] = yf;
+        }
+      }
+      continue;
+    }
     // x pass: Mx on u1, u3, u5, u6 and Kx on u6
     for (int e = t; e < NXP; e += blockDim.x) {
       const int ex = e % TX, ey = (e / TX) % HY, ez = e / (TX * HY);
@@ -329,7 +389,7 @@ double tile_work(const DevProblem& p) {
   return tiles * (25.0 * Tl::NH + 30.0 * Tl::NXP + 36.0 * Tl::NYP + 138.0 * Tl::kThreads);
 }
 
-template <typename T, typename Tl>
+template <typename T, typename Tl, bool kP1 = false>
 void launch_shape(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
   const int tx = (p.nx + Tl::TX - 1) / Tl::TX, ty = (p.ny + Tl::TY - 1) / Tl::TY, tz = (p.nz + Tl::TZ - 1) / Tl::TZ;
   dim3 grid(tx * ty * tz, (p.M + 1 + NT - 1) / NT);
@@ -340,15 +400,17 @@ void launch_shape(const DevProblem& p, const T* x, T* y, const double* b, cudaSt
   LevelW<T> w;
   w.init(p.tau, p.theta, p.beta1, p.beta2);
   // (the dynamic shared-memory limits are raised once, in matvec_prepare)
+  constexpr size_t smem = mv_smem<T, Tl, kP1>();
   if (p.reg != 0)
-    matvec_tiled<T, true, Tl><<<grid, Tl::kThreads, mv_smem<T, Tl>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+    matvec_tiled<T, true, Tl, kP1><<<grid, Tl::kThreads, smem, s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
   else
-    matvec_tiled<T, false, Tl><<<grid, Tl::kThreads, mv_smem<T, Tl>(), s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
+    matvec_tiled<T, false, Tl, kP1><<<grid, Tl::kThreads, smem, s>>>(p, x, y, b, tx, ty, ax, ay, az, w);
 }
 
 template <typename T>
 void launch_tiled(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
-  if (tile_work<TileB>(p) < tile_work<TileA>(p)) launch_shape<T, TileB>(p, x, y, b, s);
+  if (p.elem == KKT_ELEM_P1) launch_shape<T, TileA, true>(p, x, y, b, s);
+  else if (tile_work<TileB>(p) < tile_work<TileA>(p)) launch_shape<T, TileB>(p, x, y, b, s);
   else launch_shape<T, TileA>(p, x, y, b, s);
 }
 
@@ -382,11 +444,22 @@ kkt_status prepare_shape() {
   return KKT_OK;
 }
 
+template <typename T>
+kkt_status prepare_p1() {
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<T, false, TileA, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T, TileA, true>()));
+  KKT_TRY_CUDA(cudaFuncSetAttribute(matvec_tiled<T, true, TileA, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mv_smem<T, TileA, true>()));
+  return KKT_OK;
+}
+
 kkt_status matvec_prepare() {
   KKT_TRY((prepare_shape<double, TileA>()));
   KKT_TRY((prepare_shape<double, TileB>()));
   KKT_TRY((prepare_shape<float, TileA>()));
   KKT_TRY((prepare_shape<float, TileB>()));
+  KKT_TRY((prepare_p1<double>()));
+  KKT_TRY((prepare_p1<float>()));
   return KKT_OK;
 }
 

@@ -113,7 +113,7 @@ extern "C" const char* kkt_version(void) { return "stkkt 0.1 (sm_103a)"; }
 DevProblem kkt_problem::dev() const {
   DevProblem d;
   d.nx = nx; d.ny = ny; d.nz = nz; d.N = N; d.M = M; d.L = L; d.P = P;
-  d.tau = tau; d.theta = theta; d.beta1 = beta1; d.beta2 = beta2; d.reg = reg;
+  d.tau = tau; d.theta = theta; d.beta1 = beta1; d.beta2 = beta2; d.reg = reg; d.elem = elem;
   d.hx = hx; d.hy = hy; d.hz = hz;
   const size_t c = (size_t)kStencil * N;
   d.S = coef64; d.ST = coef64 + c; d.B = coef64 + 2 * c; d.K = coef64 + 3 * c;
@@ -180,6 +180,89 @@ __global__ void assemble_stencils(CellGeom g, const double* __restrict__ a_cell,
   }
 }
 
+// 8x8 matrices of one cell, local node l = lx + 2 ly + 4 lz:
+//   Me[a][b] = int phi_a phi_b,  Ke[a][b] = int grad phi_a . grad phi_b,
+//   G[d][a][b] = int (d phi_b / d x_d) phi_a.
+struct CellMats {
+  double Me[64], Ke[64], G[3][64];
+};
+
+// P1 elements on the Kuhn split of the cell (Sec. 3.1: piecewise-linear
+// elements on a regular triangulation).  For each ordering (i, j, k) of the
+// axes the tetrahedron {1 >= x_i/h_i >= x_j/h_j >= x_k/h_k >= 0} has the
+// vertices 0, e_i, e_i + e_j, (1,1,1) and the barycentric coordinates
+//   1 - s_i,  s_i - s_j,  s_j - s_k,  s_k      (s = x / h),
+// whose gradients are constant.  With |T| = hx hy hz / 6 the closed forms are
+//   mass |T| (1 + delta_ab) / 20,  stiffness |T| grad l_a . grad l_b,
+//   convection |T| / 4 * d l_b / d x_d  (the mean of l_a is 1/4).
+CellMats p1_cell_matrices(double hx, double hy, double hz) {
+  CellMats m{};
+  const double h[3] = {hx, hy, hz};
+  const double T = hx * hy * hz / 6.0;
+  const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (const auto& pm : perm) {
+    const int i = pm[0], j = pm[1], k = pm[2];
+    const int node[4] = {0, 1 << i, (1 << i) | (1 << j), 7};
+    double g[4][3] = {};
+    g[0][i] = -1.0 / h[i];
+    g[1][i] = 1.0 / h[i];
+    g[1][j] = -1.0 / h[j];
+    g[2][j] = 1.0 / h[j];
+    g[2][k] = -1.0 / h[k];
+    g[3][k] = 1.0 / h[k];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        const int ab = node[a] * 8 + node[b];
+        m.Me[ab] += T * (a == b ? 2.0 : 1.0) / 20.0;
+        m.Ke[ab] += T * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+        for (int d = 0; d < 3; ++d) m.G[d][ab] += 0.25 * T * g[b][d];
+      }
+  }
+  return m;
+}
+
+// One thread per node: the stencils from the cell matrices of the (up to 8)
+// cells around the node, with a and v constant per cell.
+__global__ void assemble_from_cells(CellGeom g, CellMats cm, const double* __restrict__ a_cell,
+                                    const double* __restrict__ v_cell, double* __restrict__ S,
+                                    double* __restrict__ ST, double* __restrict__ B, double* __restrict__ K) {
+  const int N = g.nx * g.ny * g.nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int ix = i % g.nx, iy = (i / g.nx) % g.ny, iz = i / (g.nx * g.ny);
+  double s[kStencil], st[kStencil], b[kStencil], k[kStencil];
+  for (int d = 0; d < kStencil; ++d) s[d] = st[d] = b[d] = k[d] = 0.0;
+  for (int ez = iz - 1; ez <= iz; ++ez) {
+    if (ez < 0 || ez >= g.cz) continue;
+    for (int ey = iy - 1; ey <= iy; ++ey) {
+      if (ey < 0 || ey >= g.cy) continue;
+      for (int ex = ix - 1; ex <= ix; ++ex) {
+        if (ex < 0 || ex >= g.cx) continue;
+        const int e = ex + g.cx * (ey + g.cy * ez);
+        const double ae = a_cell[e];
+        const double vx = v_cell[3 * e], vy = v_cell[3 * e + 1], vz = v_cell[3 * e + 2];
+        const int la = (ix - ex) + 2 * (iy - ey) + 4 * (iz - ez);   // local id of the test node
+        for (int lb = 0; lb < 8; ++lb) {
+          const int bx = lb & 1, by = (lb >> 1) & 1, bz = lb >> 2;
+          const int d = (ex + bx - ix + 1) + 3 * (ey + by - iy + 1) + 9 * (ez + bz - iz + 1);
+          const int ab = la * 8 + lb, ba = lb * 8 + la;
+          const double kab = cm.Ke[ab];
+          s[d] += ae * kab + vx * cm.G[0][ab] + vy * cm.G[1][ab] + vz * cm.G[2][ab];
+          st[d] += ae * kab + vx * cm.G[0][ba] + vy * cm.G[1][ba] + vz * cm.G[2][ba];
+          b[d] += cm.Me[ab];
+          k[d] += kab;
+        }
+      }
+    }
+  }
+  for (int d = 0; d < kStencil; ++d) {
+    S[(size_t)d * N + i] = s[d];
+    ST[(size_t)d * N + i] = st[d];
+    B[(size_t)d * N + i] = b[d];
+    K[(size_t)d * N + i] = k[d];
+  }
+}
+
 __global__ void to_float(const double* __restrict__ x, float* __restrict__ y, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
@@ -213,6 +296,47 @@ __global__ void source_kernel(const double* __restrict__ U, double* __restrict__
 }
 
 }  // namespace
+
+// S, ST, B, K of the problem's element from its host a and v (FP64), and the
+// FP32 copies; synchronous.
+kkt_status assemble_coefficients(kkt_problem* p, const char* who) {
+  const kkt_grid* g = &p->grid;
+  const size_t ncell = (size_t)g->cx * g->cy * g->cz;
+  const long long N = p->N;
+  const size_t ncoef = 4 * (size_t)kStencil * N;
+  double *d_a = nullptr, *d_v = nullptr;
+  if (cudaMalloc(&d_a, ncell * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&d_v, 3 * ncell * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d_a);
+    set_error(std::string(who) + ": device allocation failed");
+    return KKT_ERR_NOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d_a, p->a_cell.data(), ncell * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_v, p->v_cell.data(), 3 * ncell * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    CellGeom geo{g->cx, g->cy, g->cz, p->nx, p->ny, p->nz, p->hx, p->hy, p->hz};
+    const size_t c = (size_t)kStencil * N;
+    const unsigned blocks = (unsigned)((N + 127) / 128);
+    if (p->elem == KKT_ELEM_P1)
+      assemble_from_cells<<<blocks, 128>>>(geo, p1_cell_matrices(p->hx, p->hy, p->hz), d_a, d_v, p->coef64,
+                                           p->coef64 + c, p->coef64 + 2 * c, p->coef64 + 3 * c);
+    else
+      assemble_stencils<<<blocks, 128>>>(geo, d_a, d_v, p->coef64, p->coef64 + c, p->coef64 + 2 * c,
+                                         p->coef64 + 3 * c);
+    to_float<<<1024, 256>>>(p->coef64, p->coef32, ncoef);
+    KKT_COUNT(2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_a);
+  cudaFree(d_v);
+  if (e != cudaSuccess) {
+    set_error(std::string(who) + ": " + cudaGetErrorString(e));
+    return KKT_ERR_CUDA;
+  }
+  return KKT_OK;
+}
 
 kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_cell, const double* v_cell,
                           const int* sensor_node, int nsens, double beta1, double beta2, double theta,
@@ -285,17 +409,12 @@ kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_
     return st;
   };
   const size_t ncoef = 4 * (size_t)kStencil * N;
-  double *d_a = nullptr, *d_v = nullptr;
   if (cudaMalloc(&p->coef64, ncoef * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&p->coef32, ncoef * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&p->dir, N) != cudaSuccess || cudaMalloc(&p->sens, N * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&p->sens_ptr, (N + 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&p->sens_idx, std::max(nsens, 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&d_a, ncell * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&d_v, 3 * (size_t)ncell * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&p->sens_idx, std::max(nsens, 1) * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(d_a);
-    cudaFree(d_v);
     set_error("kkt_create: device allocation failed");
     return fail(KKT_ERR_NOMEM);
   }
@@ -304,23 +423,13 @@ kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_
   if (e == cudaSuccess) e = cudaMemcpy(p->sens, sens.data(), N * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->sens_ptr, sptr.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nsens > 0) e = cudaMemcpy(p->sens_idx, sidx.data(), nsens * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_a, a_cell, ncell * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_v, v_cell, 3 * (size_t)ncell * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    CellGeom geo{g->cx, g->cy, g->cz, (int)nx, (int)ny, (int)nz, p->hx, p->hy, p->hz};
-    const size_t c = (size_t)kStencil * N;
-    assemble_stencils<<<(unsigned)((N + 127) / 128), 128>>>(geo, d_a, d_v, p->coef64, p->coef64 + c,
-                                                            p->coef64 + 2 * c, p->coef64 + 3 * c);
-    to_float<<<1024, 256>>>(p->coef64, p->coef32, ncoef);
-    KKT_COUNT(2);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(d_a);
-  cudaFree(d_v);
   if (e != cudaSuccess) {
     set_error(std::string("kkt_create: ") + cudaGetErrorString(e));
     return fail(KKT_ERR_CUDA);
+  }
+  {
+    const kkt_status as = assemble_coefficients(p, "kkt_create");
+    if (as != KKT_OK) return fail(as);
   }
   {
     const kkt_status ms = matvec_prepare();
@@ -343,6 +452,20 @@ extern "C" kkt_status kkt_set_regularization(kkt_problem* p, int reg) {
   }
   p->reg = reg;
   return KKT_OK;
+}
+
+extern "C" kkt_status kkt_set_element(kkt_problem* p, int elem) {
+  if (!p || (elem != KKT_ELEM_Q1 && elem != KKT_ELEM_P1)) {
+    set_error("kkt_set_element: null problem, or elem not KKT_ELEM_Q1 or KKT_ELEM_P1");
+    return KKT_ERR_ARG;
+  }
+  if (elem == p->elem) return KKT_OK;
+  const int old = p->elem;
+  p->elem = elem;
+  const kkt_status st = assemble_coefficients(p, "kkt_set_element");
+  if (st != KKT_OK) p->elem = old;   // the coefficients may be partly written: reassemble the old ones
+  if (st != KKT_OK) assemble_coefficients(p, "kkt_set_element");
+  return st;
 }
 
 extern "C" kkt_status kkt_sizes(const kkt_problem* p, int* nx, int* ny, int* nz, int* levels, long long* unknowns) {

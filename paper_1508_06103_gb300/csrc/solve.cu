@@ -273,6 +273,7 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
   kkt_status st = create_problem(&cg, cnt, fine->tau * c->rt, ac.data(), vc.data(), sc.empty() ? nullptr : sc.data(),
                                  (int)sc.size(), fine->beta1, fine->beta2, fine->theta, &c->cp);
   if (st == KKT_OK) c->cp->reg = fine->reg;   // the coarse operator is the same discretisation
+  if (st == KKT_OK && fine->elem != KKT_ELEM_Q1) st = kkt_set_element(c->cp, fine->elem);
   if (st == KKT_OK) st = ras_create(&c->cp, 1, nsub_c, c_overlap, 0, factor_prec, nullptr, &c->cras);
   // The coarse GMRES keeps z_j = M_c^{-1} v_j (the flexible form's store, c_maxit
   // coarse vectors) and forms y_c = Z y: for its fixed preconditioner this is
