@@ -434,6 +434,19 @@ def gpu_arm(args):
     mv64_bytes = prob.n * 16 + coef_bytes * 8
     mv32_bytes = prob.n * 8 + coef_bytes * 4
 
+    # ---- P1 elements on the Kuhn split, same workload: mixed-form solve and matvecs --
+    # (the observations enter b only, so the Q1 forward solve's data serve here too)
+    prob.set_element("p1")
+    ras1, co1 = make(32)
+    step(ras1, co1, cobs)
+    p1_ms = timed(lambda: step(ras1, co1, cobs), args.fp64_steps)
+    p1 = dict(last)
+    del ras1, co1
+    p1_mv64_ms = timed(lambda: prob.apply(xm, ym), reps)
+    p1_mv32_ms = timed(lambda: prob.apply(xs, ys), reps)
+    prob.set_element("q1")
+    p1_coef = 4 * 15 * prob.N   # the 15 offsets the split couples
+
     peak, peak_kind = measured_peaks()
     traffic = {k: read_traffic(k) for k in ("ras_solve", "ilu0_factor", "matvec_tiled")}
     # algorithmic bytes per launch (unpadded values: no chunk padding or unit rows counted)
@@ -481,6 +494,11 @@ def gpu_arm(args):
                    "fp64_frac": mv64_bytes / (mv64_ms * 1e-3) / 1e9 / peak,
                    "fp32_frac": mv32_bytes / (mv32_ms * 1e-3) / 1e9 / peak,
                    "bytes_fp64": mv64_bytes, "bytes_fp32": mv32_bytes},
+        "p1_form": {"s_per_solve": p1_ms / 1e3, "iterations": p1.get("iters"), "true_relres": p1.get("relres"),
+                    "steps": args.fp64_steps, "matvec_fp64_us": p1_mv64_ms * 1e3,
+                    "matvec_fp32_us": p1_mv32_ms * 1e3,
+                    "matvec_fp32_frac": (prob.n * 8 + p1_coef * 4) / (p1_mv32_ms * 1e-3) / 1e9 / peak,
+                    "element": "P1 on the Kuhn split of every cell, mixed form (FP32 factors)"},
         "roofline": roof,
         "kernels": table,
         "gpu_launches": int(launches),
@@ -859,6 +877,69 @@ def examples_arm(args):
         prob.close()
 
 
+def reduced_arm(args):
+    """The reduced-space ("traditional") method of Sec. 1 on the same GPU and workload as the
+    all-at-once benchmark (32^3 x 64 by default): f is the only unknown, each application of the
+    reduced operator is a forward and a backward march of 64 spatial solves.  Solved to the same
+    true KKT relative residual (1e-8) as the all-at-once form; one JSON line with its time beside
+    the all-at-once FP64 and mixed forms' times on the same data.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    build.build()
+    c = args.cells
+    w = W.mid() if c == 32 else W.mid(cells=(c, c, c), M=args.levels, coarse_cells=(c // 2,) * 3,
+                                      coarse_M=args.levels // 2)
+    prob = api.Problem.from_workload(w)
+    if w.M == 64 and c == 32:
+        cobs = torch.from_numpy(np.loadtxt(obs_file(args), ndmin=2)).cuda()
+    else:
+        rng = np.random.Generator(np.random.PCG64(17))
+        cobs = torch.from_numpy(rng.standard_normal((w.M + 1, len(w.sensor_xyz)))).cuda()
+    b = prob.rhs(cobs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": w.name, "unknowns": prob.n, "method": "reduced space (Sec. 1), FP64"}
+    # reduced system to 1e-9 relative residual, steps to 1e-12: the KKT residual then meets 1e-8
+    torch.cuda.synchronize()
+    e0.record()
+    U, st, its, rel, stats = api.reduced_solve(prob, cobs, restart=30, rtol=args.reduced_rtol, maxit=2000,
+                                               step_rtol=1e-12)
+    e1.record()
+    torch.cuda.synchronize()
+    r = prob.residual(b, U)
+    out.update({"s_per_solve": e0.elapsed_time(e1) / 1e3, "status": st, "outer_iterations": its,
+                "reduced_relres": rel, "true_kkt_relres": float(r.norm() / b.norm()), **stats,
+                "step_iterations_mean": stats["step_iterations"] / max(1, stats["step_solves"])})
+    # the all-at-once forms on the same data
+    for prec in (64, 32):
+        ras = api.RAS(prob, w.nsub, w.overlap, prec)
+        co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.coarse_split, w.coarse_overlap, w.coarse_rtol,
+                        w.coarse_maxit, prec)
+        x = torch.zeros_like(b)
+        api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=w.restart, rtol=w.rtol, maxit=3000)
+        x.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        co.refactor_with(ras)
+        _, st2, its2, rel2 = api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=w.restart, rtol=w.rtol,
+                                             maxit=3000)
+        e1.record()
+        torch.cuda.synchronize()
+        f_a = prob.recover_source(x)
+        f_r = prob.recover_source(U)
+        out[f"all_at_once_fp{prec}"] = {"s_per_solve": e0.elapsed_time(e1) / 1e3, "iterations": its2,
+                                       "true_relres": rel2,
+                                       "f_rel_diff_vs_reduced": float((f_a - f_r).norm() / f_r.norm())}
+        ras.close()
+        co.close()
+    out["speedup_mixed_vs_reduced"] = out["s_per_solve"] / out["all_at_once_fp32"]["s_per_solve"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -885,7 +966,9 @@ def main():
                     help="--workload large: FGMRES iteration limit of a step (the solve converges slowly)")
     ap.add_argument("--coarse-levels", type=int, default=0,
                     help="--workload large: time steps of the coarse level (0: the workload's)")
-    ap.add_argument("--workload", choices=["mid", "large", "batch", "examples"], default="mid",
+    ap.add_argument("--reduced-rtol", type=float, default=1e-9,
+                    help="--workload reduced: relative residual of the reduced system")
+    ap.add_argument("--workload", choices=["mid", "large", "batch", "examples", "reduced"], default="mid",
                     help="large: time the 64^3 x 128 single solve; batch: eight independent problems solved "
                          "together; instead of the default benchmark")
     args = ap.parse_args()
@@ -895,6 +978,8 @@ def main():
         batch_arm(args)
     elif args.workload == "examples":
         examples_arm(args)
+    elif args.workload == "reduced":
+        reduced_arm(args)
     elif args.kernel == "sweep":
         sweep_arm(args)
     elif args.kernel:

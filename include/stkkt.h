@@ -340,6 +340,39 @@ kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* c, const do
                        double* true_relres, void* stream);
 
 /*
+ * reduced_solve -- the KKT solution by the reduced-space ("traditional")
+ *   method of Sec. 1, the approach the all-at-once solve is compared with: f
+ *   is the only unknown, and every application of the reduced operator
+ *     H f = W f - D G_lin(C_lin(f)),  W = beta1 Lt (x) B + beta2 Mt (x) K
+ *     (H1-L2: Mt (x) B),  D = Mt (x) B   (the f rows of the Appendix)
+ *   is a forward march of the M state steps of Eq. 8 and a backward march of
+ *   the M adjoint steps.  H f = D G0 (G0: the adjoint of the state from c0
+ *   against the data) is solved by GMRES(restart), right-preconditioned by
+ *   P = W + sigma Mt (x) B applied by fast diagonalisation (exact for trilinear
+ *   elements; an approximation under P1), to relative residual rtol or maxit
+ *   iterations; then U = (C, G, f) with the state and adjoint of f.  Each
+ *   spatial step (B + theta tau S, or S^T; identity rows on Dirichlet nodes)
+ *   is solved by Jacobi-preconditioned GMRES(40) on the device to relative
+ *   residual step_rtol, from the neighbouring level.
+ *   c_obs  device FP64, (M+1) x nsens sensor values (may be NULL if nsens == 0);
+ *   c0     device FP64, N initial state values, or NULL (zero);
+ *   U      device FP64, 3 N (M+1): the KKT solution, point-block order;
+ *   iters, relres  host: outer GMRES iterations and relative residual of the
+ *          reduced system (may be NULL);
+ *   stats  host, 4 values (may be NULL): applications of H, step solves, step
+ *          GMRES iterations in total, the most in one step solve.
+ *   Allocates its workspace for the call (restart + 1 vectors of N (M+1)
+ *   values, 6 N (M+1) more, 2 x 41 level vectors) and synchronises the stream
+ *   once per step solve.  Returns OK, NOT_CONVERGED (outer iteration limit) or
+ *   BREAKDOWN (outer Krylov breakdown) with U written, or an error; a step
+ *   solve that misses step_rtol within 2,000 iterations returns NOT_CONVERGED
+ *   (BREAKDOWN on a breakdown) before U is written.
+ */
+kkt_status reduced_solve(kkt_problem* p, const double* c_obs, const double* c0, double* U, int restart,
+                         double rtol, int maxit, double step_rtol, int* iters, double* relres,
+                         long long stats[4], void* stream);
+
+/*
  * gmres_solve_batch -- flexible GMRES(restart) on several independent problems
  *   at once, right-preconditioned by their ras_setup_batch preconditioner m
  *   (probs in the same order): b, x device FP64 vectors over the concatenated

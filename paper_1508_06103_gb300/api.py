@@ -275,6 +275,23 @@ def gmres_solve(prob: Problem, b: torch.Tensor, x: Optional[torch.Tensor] = None
     return x, st, it.value, rel.value
 
 
+def reduced_solve(prob: Problem, c_obs: torch.Tensor, c0: Optional[torch.Tensor] = None, restart: int = 30,
+                  rtol: float = 1e-10, maxit: int = 2000, step_rtol: float = 1e-13, stream=None):
+    """KKT solution by the reduced-space method (reduced_solve); returns
+    (U, status, outer iterations, reduced relative residual, stats dict)."""
+    lib = _lib.load()
+    U = prob.zeros()
+    it = C.c_int()
+    rel = C.c_double()
+    stats = (C.c_longlong * 4)()
+    st = lib.reduced_solve(prob.h, _ptr(c_obs) if prob.nsens else None, _ptr(c0) if c0 is not None else None,
+                           _ptr(U), int(restart), float(rtol), int(maxit), float(step_rtol), C.byref(it),
+                           C.byref(rel), stats, _stream(stream))
+    check(st, "reduced_solve")
+    names = ("hess_applies", "step_solves", "step_iterations", "step_iterations_max")
+    return U, st, it.value, rel.value, dict(zip(names, list(stats)))
+
+
 def _handles(probs: Sequence[Problem]):
     return (C.c_void_p * len(probs))(*[p.h.value for p in probs])
 

@@ -138,7 +138,7 @@ struct KktOp : Operator {
     d.gate = gate;
     return launch_matvec64(d, x, y, s);
   }
-  unsigned long long uid() const override { return p->uid * 4 + (unsigned long long)p->reg; }
+  unsigned long long uid() const override { return p->uid * 4 + (unsigned long long)(p->reg + 2 * p->elem); }
 };
 
 // The coarse operator inside the preconditioner: FP64, or FP32 arithmetic on
@@ -154,7 +154,7 @@ struct CoarseOp : Operator {
     if (prec == 64) return launch_matvec64(d, x, y, s);
     return launch_matvec32_d(d, x, y, x32, y32, s);
   }
-  unsigned long long uid() const override { return p->uid * 4 + (unsigned long long)p->reg; }
+  unsigned long long uid() const override { return p->uid * 4 + (unsigned long long)(p->reg + 2 * p->elem); }
 };
 
 struct RasOp : Operator {
