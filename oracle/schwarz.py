@@ -12,8 +12,9 @@ Test infrastructure (see the package header).
   the homogeneous Dirichlet conditions Eqs. 11-12 on the cut faces.
 * Local solvers: ILU(0) on the structural pattern of F_h (the stencil of
   each block row, textbook IKJ order), ILU(k) (the same elimination on the
-  pattern grown by levels of fill up to k, Table 1), or exact sparse LU
-  (scipy, as one step).
+  pattern grown by levels of fill up to k, Table 1), the 3x3 point-block
+  ILU(0) (the same elimination on the pattern of whole point blocks, Sec. 3.2's
+  point-block ordering), or exact sparse LU (scipy, as one step).
 * One-level restricted additive Schwarz, the cited Cai-Sarkis form
       z = sum_ij (R^0_ij)^T  M_ij^{-1}  R^delta_ij r
   (restricted prolongation); variant="harmonic" gives the literal operand
@@ -32,7 +33,9 @@ on the pattern, ILU(0) = LU without fill, one box with exact LU = exact
 inverse, interpolation reproduces multilinear functions, <Pu, w> = <u, P^T w>,
 coarse mesh equal to fine mesh with an exact coarse solve is exact; ILU(k):
 the textbook fill diagonals of the 5-point Laplacian for k = 1, 2, the ILU
-property on the level-1 pattern of a KKT box, exact LU at a high level).
+property on the level-1 pattern of a KKT box, exact LU at a high level;
+point-block ILU(0): whole 3x3 blocks of the 81-point neighbourhood, exact LU
+on a box of one spatial node, where the block matrix is block tridiagonal).
 """
 
 from __future__ import annotations
@@ -227,6 +230,33 @@ def local_pattern(p: kkt.Problem, idx: np.ndarray, rows: int | None = None) -> L
     return out
 
 
+def block_pattern(p: kkt.Problem, idx: np.ndarray) -> List[np.ndarray]:
+    """Pattern of the 3x3 point-block ILU(0) on the unknowns idx (local numbering).
+
+    The point-block order (Sec. 3.2) groups the unknowns C, G, f of a space-time
+    point into a 3x3 block; block (p, q) belongs to the pattern when some entry
+    of F_h couples the two points, i.e. q is one of the 27 spatial neighbours of
+    p at levels n-1, n, n+1.  Every entry of such a block is kept, so the
+    incomplete factorisation on this pattern is the block ILU(0) whose diagonal
+    blocks are factored exactly (no fill is dropped inside a block).
+    """
+    pos = {int(g): k for k, g in enumerate(idx)}
+    out = []
+    for g in idx:
+        n, j = divmod(int(g // 3), p.N)
+        # the f row of a point is never an identity row and reaches every point
+        # its C and G rows reach (levels n-1..n+1, the 27 neighbours)
+        pts = {(m, k) for (m, k, _) in kkt.structural_pattern_row(p, n, j, 2)}
+        cols = []
+        for (m, k) in pts:
+            for cc in range(3):
+                gi = (m * p.N + k) * 3 + cc
+                if gi in pos:
+                    cols.append(pos[gi])
+        out.append(np.array(sorted(cols), dtype=np.int64))
+    return out
+
+
 class RAS:
     """One-level space-time restricted additive Schwarz preconditioner."""
 
@@ -241,6 +271,8 @@ class RAS:
             Aloc = F[idx][:, idx].tocsr()
             if local == "ilu0":
                 solver = ILU0(Aloc, local_pattern(p, idx))
+            elif local == "bilu0":   # 3x3 point-block ILU(0)
+                solver = ILU0(Aloc, block_pattern(p, idx))
             elif local.startswith("ilu"):   # "ilu1", "ilu2", ...: ILU(k) on the level-k pattern
                 solver = ILU0(Aloc, iluk_pattern(Aloc, local_pattern(p, idx), int(local[3:])))
             elif local == "lu":

@@ -297,3 +297,62 @@ def test_higher_fill_level_needs_no_more_iterations():
     its = [krylov.gmres(lambda u: F @ u, bvec, schwarz.RAS(p, F, (2, 2, 2, 2), 1, loc).apply, restart=60,
                         rtol=1e-8).iterations for loc in ("ilu0", "ilu1", "lu")]
     assert its[0] >= its[1] >= its[2], its
+
+
+# ---------------------------------------------------------------------------
+# point-block ILU(0)
+# ---------------------------------------------------------------------------
+
+def test_block_pattern_holds_whole_blocks_of_the_81_point_neighbourhood():
+    p, F = _small(cells=(3, 3, 2), M=3)
+    b = schwarz.boxes(p, (1, 1, 1, 1), 0)[0]
+    idx, _ = schwarz.box_unknowns(p, b)
+    pat = schwarz.block_pattern(p, idx)
+    scal = schwarz.local_pattern(p, idx)
+    nx, ny, nz = p.nodes
+    for i, g in enumerate(idx):
+        n, j = divmod(int(g // 3), p.N)
+        ix, iy, iz = j % nx, (j // nx) % ny, j // (nx * ny)
+        cnt = 1
+        for lo, hi, v in ((0, p.M, n), (0, nx - 1, ix), (0, ny - 1, iy), (0, nz - 1, iz)):
+            cnt *= min(hi, v + 1) - max(lo, v - 1) + 1
+        assert len(pat[i]) == 3 * cnt                            # all three components of every neighbour
+        assert set(scal[i].tolist()) <= set(pat[i].tolist())     # contains the scalar pattern
+        assert set((pat[i] // 3).tolist()) == set((pat[i - i % 3] // 3).tolist())   # same points for C, G, f
+
+
+def test_block_ilu0_is_exact_on_boxes_of_one_spatial_node():
+    """A box of one node over all levels couples point n only to n-1 and n+1: its
+    block matrix is block tridiagonal, block LU makes no fill outside it, so the
+    point-block ILU(0) is the exact inverse (scalar ILU(0) is not: it drops fill
+    inside the blocks)."""
+    p, F = _small(cells=(2, 2, 1), M=4)
+    nx, ny, nz = p.nodes
+    r = W.random_vector(p.n, 6)
+    zb = schwarz.RAS(p, F, (nx, ny, nz, 1), 0, "bilu0").apply(r)
+    zl = schwarz.RAS(p, F, (nx, ny, nz, 1), 0, "lu").apply(r)
+    zs = schwarz.RAS(p, F, (nx, ny, nz, 1), 0, "ilu0").apply(r)
+    np.testing.assert_allclose(zb, zl, rtol=1e-10, atol=1e-12 * np.abs(zl).max())
+    assert np.abs(zs - zl).max() > 1e-6 * np.abs(zl).max()
+
+
+def test_block_ilu0_has_the_ilu_property_on_its_pattern():
+    p, F = _small()
+    b = schwarz.boxes(p, (2, 1, 1, 2), 1)[1]
+    idx, _ = schwarz.box_unknowns(p, b)
+    A = F[idx][:, idx].tocsr()
+    pat = schwarz.block_pattern(p, idx)
+    ilu = schwarz.ILU0(A, pat)
+    n = len(idx)
+    Lm, Um = np.eye(n), np.zeros((n, n))
+    for i in range(n):
+        for k, v in ilu.L[i].items():
+            Lm[i, k] = v
+        Um[i, i] = ilu.diag[i]
+        for j, v in ilu.U[i].items():
+            Um[i, j] = v
+    mask = np.zeros((n, n), dtype=bool)
+    for i, cols in enumerate(pat):
+        mask[i, cols] = True
+    Ad = A.toarray()
+    assert np.abs((Lm @ Um - Ad)[mask]).max() < 1e-13 * np.abs(Ad).max()
