@@ -877,6 +877,55 @@ def examples_arm(args):
         prob.close()
 
 
+def table1_arm(args):
+    """The paper's Table 1 experiment on this workload family: the two-level method with the
+    fine subdomains factored by ILU(0), ILU(1) or the 3x3 point-block ILU(0) (coarse level:
+    ILU(0)), FP32 factors inside FP64 FGMRES(30) to 1e-8.  One JSON line per local solver:
+    iterations, refactorisation and solve times (CUDA events), factor values per point.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1508_06103_gb300 import api, build
+    from paper_1508_06103_gb300 import workloads as W
+
+    build.build()
+    c, M = args.cells, args.levels
+    w = W.mid(cells=(c, c, c), M=M, coarse_cells=(c // 2,) * 3, coarse_M=M // 2)
+    prob = api.Problem.from_workload(w)
+    rng = np.random.Generator(np.random.PCG64(17))
+    cobs = torch.from_numpy(rng.standard_normal((w.M + 1, len(w.sensor_xyz)))).cuda()
+    b = prob.rhs(cobs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    for local in args.locals.split(","):
+        ras = api.RAS(prob, w.nsub, w.overlap, args.prec, local=local)
+        co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.coarse_split, w.coarse_overlap, w.coarse_rtol,
+                        w.coarse_maxit, args.prec)
+        fac_ms, _ = timed(lambda: ras.refactor())
+        x = torch.zeros_like(b)
+        api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=30, rtol=1e-8, maxit=3000)   # warm-up
+        x.zero_()
+        sol_ms, res = timed(lambda: api.gmres_solve(prob, b, x, ras=ras, coarse=co, restart=30, rtol=1e-8,
+                                                    maxit=3000))
+        _, st, its, rel = res
+        info = ras.info()
+        print(json.dumps({"table": 1, "workload": w.name, "local": local, "factor_prec": args.prec,
+                          "iterations": its, "status": st, "true_relres": rel, "refactor_fine_ms": fac_ms,
+                          "solve_ms": sol_ms, "factor_values": info.get("factor_values"),
+                          "box_points": info.get("points")}), flush=True)
+        ras.close()
+        co.close()
+
+
 def reduced_arm(args):
     """The reduced-space ("traditional") method of Sec. 1 on the same GPU and workload as the
     all-at-once benchmark (32^3 x 64 by default): f is the only unknown, each application of the
@@ -948,7 +997,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["ras", "matvec", "sweep", "peaks"], default=None,
+    ap.add_argument("--kernel", choices=["ras", "matvec", "sweep", "peaks", "table1"], default=None,
                     help="time one kernel on a member of the workload family instead of the full solve; "
                          "sweep: overlap and one/two-level sweep of the mixed-form solve")
     ap.add_argument("--cells", type=int, default=32)
@@ -966,6 +1015,8 @@ def main():
                     help="--workload large: FGMRES iteration limit of a step (the solve converges slowly)")
     ap.add_argument("--coarse-levels", type=int, default=0,
                     help="--workload large: time steps of the coarse level (0: the workload's)")
+    ap.add_argument("--locals", default="ilu0,ilu1,bilu0",
+                    help="--kernel table1: fine local solvers (ilu0, ilu1, bilu0)")
     ap.add_argument("--reduced-rtol", type=float, default=1e-9,
                     help="--workload reduced: relative residual of the reduced system")
     ap.add_argument("--workload", choices=["mid", "large", "batch", "examples", "reduced"], default="mid",
@@ -982,6 +1033,8 @@ def main():
         reduced_arm(args)
     elif args.kernel == "sweep":
         sweep_arm(args)
+    elif args.kernel == "table1":
+        table1_arm(args)
     elif args.kernel:
         kernel_arm(args)
     elif args.impl == "reference":

@@ -161,6 +161,15 @@ kkt_status kkt_apply(kkt_problem* p, const void* x, void* y, int precision, void
 kkt_status kkt_residual(kkt_problem* p, const double* b, const double* x, double* r, void* stream);
 
 /*
+ * ras_local_pattern -- slots per row type (C, G, f) of an interior point under a
+ *   subdomain solver: local 0 ILU(0) (F_h's structural pattern: 108, 56, 162),
+ *   2 ILU(1) (the pattern with one level of fill, Sec. 4 Table 1), 3 the 3x3
+ *   point-block ILU(0) (243 each: the 81-point neighbourhood, all components).
+ *   Host only, no device work.  Errors: ARG.
+ */
+kkt_status ras_local_pattern(int local, int counts[3]);
+
+/*
  * ras_setup -- one-level space-time restricted additive Schwarz preconditioner
  *   (Sec. 3.2): nsub[0..3] = subdomains along x, y, z and time (part k of n
  *   nodes or levels holds floor(n/p) + (k < n mod p)); each box is extended
@@ -173,7 +182,17 @@ kkt_status kkt_residual(kkt_problem* p, const double* b, const double* x, double
  *                order (FP64 only; for small boxes: at most 28,672 unknowns
  *                and half-bandwidth 2,048 per box, else KKT_ERR_ARG, and the
  *                bands must fit in 80 % of free device memory, else
- *                KKT_ERR_NOMEM).
+ *                KKT_ERR_NOMEM); 2 = ILU(1), the incomplete factorisation on
+ *                the pattern with one level of fill (Sec. 4, Table 1; per
+ *                point, so boxes near faces keep only the fill their own
+ *                elimination paths make); 3 = 3x3 point-block ILU(0), the
+ *                incomplete factorisation on the pattern of whole point
+ *                blocks of the 81-point neighbourhood (Sec. 3.2 point-block
+ *                ordering; diagonal blocks factored exactly).  2 and 3: FP64
+ *                or FP32 (factor_prec 64 or 32), one problem, factor values
+ *                stored rank-major per box (ras_local_pattern slots per row),
+ *                no static apply; their solve runs one CTA per box with a
+ *                barrier per wavefront.
  *   factor_prec  64 = factor and solve in FP64, 32 = FP32, 16 = factor in FP32
  *                and store the factors as BF16 (round to nearest); the solve
  *                converts them to FP32 and accumulates in FP32.

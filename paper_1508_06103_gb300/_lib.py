@@ -35,6 +35,7 @@ SIGNATURES = {
     "kkt_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "kkt_set_regularization": (C.c_int, [C.c_void_p, C.c_int]),
     "kkt_set_element": (C.c_int, [C.c_void_p, C.c_int]),
+    "ras_local_pattern": (C.c_int, [C.c_int, C.c_void_p]),
     "kkt_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "kkt_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ras_setup": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),

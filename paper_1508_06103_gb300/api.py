@@ -121,7 +121,8 @@ class RAS:
 
     def __init__(self, prob: Problem, nsub: Sequence[int], overlap: int, factor_prec: int = 64, local: str = "ilu0",
                  shape: Optional[Sequence[int]] = None):
-        """factor_prec 64, 32 or 16 (BF16 storage); local "ilu0" or "lu" (exact, FP64 only).
+        """factor_prec 64, 32 or 16 (BF16 storage); local "ilu0", "lu" (exact, FP64 only), "ilu1" (ILU(1))
+        or "bilu0" (3x3 point-block ILU(0)); the last two in FP64 or FP32.
 
         shape: None (chosen by the library) or (chunk points, ring buffers, lanes, placement) for
         ras_setup_shape, placement 1 = local vectors in shared memory, 2 = in global memory, 0 = any.
@@ -130,7 +131,7 @@ class RAS:
         self.prob = prob
         ns = (C.c_int * 4)(*[int(v) for v in nsub])
         h = C.c_void_p()
-        loc = {"ilu0": 0, "lu": 1}[local]
+        loc = {"ilu0": 0, "lu": 1, "ilu1": 2, "bilu0": 3}[local]
         if shape is None:
             check(self._lib.ras_setup(prob.h, ns, int(overlap), loc, int(factor_prec), C.byref(h)), "ras_setup")
         else:
@@ -273,6 +274,13 @@ def gmres_solve(prob: Problem, b: torch.Tensor, x: Optional[torch.Tensor] = None
                          int(restart), float(rtol), int(maxit), int(flex), C.byref(it), C.byref(rel), _stream(stream))
     check(st, "gmres_solve")
     return x, st, it.value, rel.value
+
+
+def local_pattern(local: str):
+    """Slots per row type (C, G, f) of an interior point under a local solver (ras_local_pattern)."""
+    counts = (C.c_int * 3)()
+    check(_lib.load().ras_local_pattern({"ilu0": 0, "ilu1": 2, "bilu0": 3}[local], counts), "ras_local_pattern")
+    return list(counts)
 
 
 def reduced_solve(prob: Problem, c_obs: torch.Tensor, c0: Optional[torch.Tensor] = None, restart: int = 30,

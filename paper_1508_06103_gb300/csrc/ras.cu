@@ -653,12 +653,17 @@ kkt_status ras_create(kkt_problem* const* probs, int nprob, const int nsub[4], i
     return KKT_ERR_ARG;
   }
   kkt_problem* p = probs[0];
-  if (overlap < 0 || (local != 0 && local != 1) || (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
-    set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)) or 1 (exact LU), factor_prec 64, 32 or 16");
+  if (overlap < 0 || local < 0 || local > 3 || (factor_prec != 64 && factor_prec != 32 && factor_prec != 16)) {
+    set_error("ras_setup: overlap must be >= 0, local 0 (ILU(0)), 1 (exact LU), 2 (ILU(1)) or 3 (point-block "
+              "ILU(0)), factor_prec 64, 32 or 16");
     return KKT_ERR_ARG;
   }
   if (local == 1 && factor_prec != 64) {
     set_error("ras_setup: the exact local LU is FP64 only (factor_prec 64)");
+    return KKT_ERR_ARG;
+  }
+  if (local >= 2 && factor_prec == 16) {
+    set_error("ras_setup: ILU(1) and point-block ILU(0) factor in FP64 or FP32 (factor_prec 64 or 32)");
     return KKT_ERR_ARG;
   }
   const SlotTables& T = tables();
@@ -930,7 +935,8 @@ kkt_status ras_create(kkt_problem* const* probs, int nprob, const int nsub[4], i
       cudaMalloc(&m->otab, std::max<size_t>(1, otab.size()) * sizeof(int2)) != cudaSuccess ||
       cudaMalloc(&m->vtab, vtab.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->chunks, chunks.size() * sizeof(Chunk)) != cudaSuccess ||
-      cudaMalloc(&m->F, foff * esz) != cudaSuccess || cudaMalloc(&m->V, voff * vsz) != cudaSuccess ||
+      cudaMalloc(&m->F, (local >= 2 ? 16 : foff) * esz) != cudaSuccess ||
+      cudaMalloc(&m->V, (local >= 2 ? 16 : voff) * vsz) != cudaSuccess ||
       (factor_prec == 16 && cudaMalloc(&m->Ffac, foff * sizeof(float)) != cudaSuccess) ||
       cudaMalloc(&m->status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&m->dprobs, m->probs.size() * sizeof(DevProblem)) != cudaSuccess)
@@ -963,12 +969,13 @@ kkt_status ras_create(kkt_problem* const* probs, int nprob, const int nsub[4], i
     e = cudaMemcpy(m->otab, otab.data(), otab.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->vtab, vtab.data(), vtab.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(m->F, 0, foff * esz);
-  if (e == cudaSuccess) e = cudaMemset(m->V, 0, voff * vsz);
+  if (e == cudaSuccess) e = cudaMemset(m->F, 0, (local >= 2 ? 16 : foff) * esz);
+  if (e == cudaSuccess) e = cudaMemset(m->V, 0, (local >= 2 ? 16 : voff) * vsz);
   if (e == cudaSuccess && m->Ffac) e = cudaMemset(m->Ffac, 0, foff * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
   if (e != cudaSuccess) return fail(KKT_ERR_CUDA, cudaGetErrorString(e));
-  kkt_status st = ras_factor(m, nullptr);
+  kkt_status st = local >= 2 ? gp_create(m, local, factor_prec) : KKT_OK;
+  if (st == KKT_OK) st = ras_factor(m, nullptr);
   if (st != KKT_OK) {
     ras_destroy(m);
     return st;
@@ -1008,7 +1015,8 @@ kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s) {
   for (size_t k = 0; k < m->probs.size(); ++k) m->dprobs_h[k] = m->probs[k]->dev();
   KKT_TRY_CUDA(cudaMemcpyAsync(m->dprobs, m->dprobs_h.data(), m->dprobs_h.size() * sizeof(DevProblem),
                                cudaMemcpyHostToDevice, s));
-  if (m->local == 1) KKT_TRY(ras_lu_factor(m, s));
+  if (m->gp) KKT_TRY(gp_factor(m, s));
+  else if (m->local == 1) KKT_TRY(ras_lu_factor(m, s));
   else if (m->prec == 64) KKT_TRY(ras_factor_launch64(m, s));
   else if (m->prec == 32) KKT_TRY(ras_factor_launch32(m, s));
   else KKT_TRY(ras_factor_launch16(m, s));
@@ -1034,6 +1042,7 @@ kkt_status ras_factor(ras_precond* m, cudaStream_t s) {
 kkt_status ras_launch(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate,
                       int gate_stride) {
   TimedScope timed(&m->timing, s);
+  if (m->gp) return gp_solve(m, r, z, s, gate);
   if (m->local == 1) return ras_lu_solve(m, r, z, s, gate);
   if (m->prec == 64) return launch_solve<double>(m, r, z, (double*)m->V, s, gate, gate_stride);
   if (m->prec == 32) return launch_solve<float>(m, r, z, (float*)m->V, s, gate, gate_stride);
@@ -1148,7 +1157,7 @@ extern "C" kkt_status ras_info(const ras_precond* m, int* nbox, long long* point
   for (const BoxDesc& b : m->boxes_h) pts += b.P;
   if (nbox) *nbox = m->nbox;
   if (points) *points = pts;
-  if (factor_values) *factor_values = m->local == 1 ? m->ab_count : m->fcount;
+  if (factor_values) *factor_values = m->local == 1 ? m->ab_count : (m->gp ? gp_factor_count(m) : m->fcount);
   if (value_bytes) *value_bytes = m->prec == 64 ? 8 : (m->prec == 32 ? 4 : 2);
   return KKT_OK;
 }
@@ -1201,6 +1210,7 @@ extern "C" void ras_destroy(ras_precond* m) {
   cudaFree(m->V);
   cudaFree(m->status);
   cudaFree(m->dprobs);
+  gp_destroy(m);
   delete m->bw;
   delete m;
 }

@@ -18,6 +18,8 @@ struct Chunk {
   long long off;               // element offset of the block within the box
 };
 
+struct GpFactor;   // ILU(1) / point-block ILU(0) factors (iluk.cu)
+
 // One subdomain box (extended set, owned set, storage offsets).
 struct BoxDesc {
   int x0, y0, z0, t0;          // origin of the extended box (global node / level)
@@ -88,6 +90,7 @@ struct ras_precond {
   TimingLog timing;            // subdomain-solve launches
   TimingLog factor_timing;     // ILU(0) factorisation launches
   BatchWork* bw = nullptr;     // gmres_solve_batch workspace (several problems)
+  GpFactor* gp = nullptr;      // local 2 (ILU(1)) or 3 (point-block ILU(0))
 };
 
 // shape: NULL, or {chunk points, ring buffers, lanes per point, vector placement
@@ -96,6 +99,12 @@ struct ras_precond {
 // largest first (so the CTAs of a launch finish together as far as they can).
 kkt_status ras_create(kkt_problem* const* probs, int nprob, const int nsub[4], int overlap, int local,
                       int factor_prec, const int* shape, ras_precond** out);
+// iluk.cu: the pattern-driven local solvers (local 2 and 3)
+kkt_status gp_create(ras_precond* m, int local, int prec);
+kkt_status gp_factor(ras_precond* m, cudaStream_t s);
+kkt_status gp_solve(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate);
+void gp_destroy(ras_precond* m);
+long long gp_factor_count(const ras_precond* m);
 kkt_status ras_factor(ras_precond* m, cudaStream_t s);          // enqueue, synchronise, check
 kkt_status ras_factor_enqueue(ras_precond* m, cudaStream_t s);  // enqueue only
 kkt_status ras_factor_status(ras_precond* m);                   // after the stream completed

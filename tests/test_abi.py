@@ -76,3 +76,27 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
     assert lib.kkt_set_element(None, 1) == -1
     assert b"kkt_set_element" in lib.kkt_last_error()
     assert lib.gmres_solve(None, None, None, None, None, 30, 1e-8, 10, 0, None, None, None) == -1
+
+
+def test_local_patterns_of_an_interior_point():
+    """Host logic of the pattern-driven local solvers (no device work): ILU(0) keeps F_h's
+    structural pattern (C: 2 levels x 27 x 2 components, G: 2 x 27 + 2 sensor couplings,
+    f: 3 x 27 x 2), the point-block ILU(0) the 81-point neighbourhood in all three components,
+    and ILU(1) the level-1 pattern, a strict superset of ILU(0)'s."""
+    from paper_1508_06103_gb300 import api
+
+    assert api.local_pattern("ilu0") == [108, 56, 162]
+    assert api.local_pattern("bilu0") == [243, 243, 243]
+    # ILU(1): the oracle's levels of fill (iluk_pattern) at the centre of a 5^4-point box with
+    # a sensor at every node and no Dirichlet face (every level-1 path stays inside)
+    import numpy as np
+    from oracle import kkt, schwarz
+
+    p = kkt.Problem((4, 4, 4), (1.0, 1.0, 1.0), 1.0, 4, 0.5, 0, np.full(64, 0.1), np.ones((64, 3)),
+                    np.arange(125), 1e-3, 1e-2)
+    box = schwarz.boxes(p, (1, 1, 1, 1), 0)[0]
+    idx, _ = schwarz.box_unknowns(p, box)
+    A = kkt.assemble(p)[idx][:, idx].tocsr()
+    pat1 = schwarz.iluk_pattern(A, schwarz.local_pattern(p, idx), 1)
+    centre = 2 + 5 * (2 + 5 * (2 + 5 * 2))
+    assert api.local_pattern("ilu1") == [len(pat1[3 * centre + c]) for c in range(3)] == [780, 199, 667]
