@@ -12,9 +12,9 @@
 // {-1, 0, 1}^4.  A point near a box face or the domain boundary uses a subset:
 // the per-point levels decide which slots it keeps.
 //
-// Values and levels.  Rank-major per box: slot s of the point in schedule
-// position q at F[foff + s * P + q] (consecutive points, consecutive
-// addresses), its level of fill at LV[...] (0 for an entry of F_h's
+// Values and levels.  Point-major per box: slot s of the point in schedule
+// position q at F[foff + q * S + s] (a warp takes one point, its lanes
+// consecutive slots), its level of fill at LV[...] (0 for an entry of F_h's
 // structural pattern, 255 for a slot the point does not have).
 //
 // Elimination (IKJ, rows in the natural point-block order, as the oracle's
@@ -28,7 +28,8 @@
 // a point lies on an earlier wavefront.
 //
 // Solve.  One CTA per box: gather R^delta r, forward and backward sweeps by
-// wavefront over the same slot lists, scatter the owned points.
+// wavefront over the same slot lists (a warp per point), scatter the owned
+// points.
 
 #include <algorithm>
 #include <array>
@@ -172,7 +173,7 @@ extern "C" kkt_status ras_local_pattern(int local, int counts[3]) {
 
 // Per-box storage of the pattern-driven factors.
 struct GpBox {
-  long long foff;   // values / levels: slot s of schedule position q at foff + s * P + q
+  long long foff;   // values / levels: slot s of schedule position q at foff + q * S + s
   long long voff;   // local vector: 3 values per point
   long long poff;   // schedule arrays (perm, iperm)
   long long loff;   // wavefront pointers
@@ -227,7 +228,8 @@ struct GpFactor {
 
 namespace {
 
-constexpr int kGpThreads = 128;
+constexpr int kGpThreads = 192;        // factor CTA (row buffers: 6 warps x 800 slots fit 48 KB in FP64)
+constexpr int kGpSolveThreads = 256;
 
 __device__ __forceinline__ int gp_row_of(const GpTables& tb, int s) {
   return s < tb.base[1] ? 0 : (s < tb.base[2] ? 1 : 2);
@@ -242,19 +244,22 @@ __device__ __forceinline__ int gp_col_lex(const BoxDesc& bx, const signed char* 
 
 // Initial values (the principal submatrix of F_h on the box, Eq. 10-12) and
 // levels (0: F_h's structural pattern; 255: not kept unless fill reaches it).
+// One warp per point, its lanes over the slots (point-major storage).
 template <typename T>
 __global__ void gp_gather(const DevProblem* __restrict__ probs, const BoxDesc* __restrict__ boxes,
                           const GpBox* __restrict__ gb, const int* __restrict__ perm, GpTables tb, T* __restrict__ F,
                           unsigned char* __restrict__ LV) {
   const BoxDesc bx = boxes[blockIdx.y];
   const GpBox g = gb[blockIdx.y];
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (q >= g.P) return;
   const DevProblem p = probs[bx.prob];
   const Coefs<T> cf = coefs<T>(p);
   const PointRow<T> pr = point_row<T>(p, bx, perm[g.poff + q]);
   const bool idC = pr.n == 0 || pr.dirj, idG = pr.n == p.M || pr.dirj;
-  for (int s = 0; s < tb.S; ++s) {
+  const long long o = g.foff + (long long)q * tb.S;
+  for (int s = lane; s < tb.S; s += 32) {
     const signed char* sl = tb.slot + 5 * s;
     const int c = gp_row_of(tb, s);
     const bool inb = gp_col_lex(bx, sl, pr.kx, pr.ky, pr.kz, pr.kt) >= 0;
@@ -269,8 +274,8 @@ __global__ void gp_gather(const DevProblem* __restrict__ probs, const BoxDesc* _
                      (c == 1 && sl[4] == 0 && pr.sj == (T)0));
     }
     const bool keep0 = tb.K == 0 ? inb : structural;   // point-block: every in-box slot
-    F[g.foff + (long long)s * g.P + q] = v;
-    LV[g.foff + (long long)s * g.P + q] = keep0 ? 0 : 255;
+    F[o + s] = v;
+    LV[o + s] = keep0 ? 0 : 255;
   }
 }
 
@@ -278,62 +283,84 @@ __device__ __forceinline__ void gp_check_pivot(double d, int* status) {
   if (!(fabs(d) > 1e-300) || !isfinite(d)) atomicExch(status, 1);
 }
 
-// One CTA per box; wavefronts in order with a barrier between them, one thread
-// per point, its C, G and f rows in turn (IKJ, see the file header).
+constexpr int kGpWarps = kGpThreads / 32;
+
+// One CTA per box; wavefronts in order with a barrier between them; one warp
+// per point, its C, G and f rows in turn (IKJ, see the file header).  The row
+// (values and levels) sits in the warp's shared memory during its
+// elimination; the L slots go in order, the update pairs of one L slot
+// (distinct targets) are split over the lanes.
 template <typename T>
 __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restrict__ boxes,
                                                         const GpBox* __restrict__ gb, const int* __restrict__ perm,
                                                         const int* __restrict__ iperm, const int* __restrict__ lptr,
                                                         GpTables tb, T* __restrict__ F, unsigned char* __restrict__ LV,
                                                         int* __restrict__ status) {
+  __shared__ T rowv[kGpWarps][kGpMaxRow];
+  __shared__ unsigned char rowl[kGpWarps][kGpMaxRow];
   const BoxDesc bx = boxes[blockIdx.x];
   const GpBox g = gb[blockIdx.x];
-  T* Fb = F + g.foff;
-  unsigned char* Lb = LV + g.foff;
   const int* ip = iperm + g.poff;
-  const long long P = g.P;
-  unsigned char lev[kGpMaxRow];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x / 32;
+  T* rv = rowv[wp];
+  unsigned char* rl = rowl[wp];
+  const int K = tb.K;
   for (int w = 0; w < g.nlev; ++w) {
     const int l0 = lptr[g.loff + w], l1 = lptr[g.loff + w + 1];
-    for (int q = l0 + threadIdx.x; q < l1; q += blockDim.x) {
+    for (int q = l0 + wp; q < l1; q += kGpWarps) {
       const int lex = perm[g.poff + q];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
+      T* own = F + g.foff + (long long)q * tb.S;
+      unsigned char* ownl = LV + g.foff + (long long)q * tb.S;
       for (int c = 0; c < 3; ++c) {
         const int b = tb.base[c], nrow = tb.cnt[c], dg = tb.diag[c];
-        for (int u = 0; u < nrow; ++u) lev[u] = Lb[(b + u) * P + q];
-        if (tb.K > 0) {   // symbolic pass: final levels of the row
+        for (int u = lane; u < nrow; u += 32) {
+          rv[u] = own[b + u];
+          rl[u] = ownl[b + u];
+        }
+        __syncwarp();
+        if (K > 0) {   // symbolic pass: final levels of the row
           for (int s = 0; s < dg; ++s) {
-            if (lev[s] > tb.K) continue;
+            const int ls = rl[s];
+            if (ls > K) continue;
             const int qp = ip[gp_col_lex(bx, tb.slot + 5 * (b + s), kx, ky, kz, kt)];
-            for (int e = tb.tptr[b + s]; e < tb.tptr[b + s + 1]; ++e) {
-              const int lp = Lb[(long long)tb.tt[e] * P + qp];
-              if (lp > tb.K) continue;
-              const int nl = lev[s] + lp + 1;
+            const unsigned char* pl = LV + g.foff + (long long)qp * tb.S;
+            for (int e = tb.tptr[b + s] + lane; e < tb.tptr[b + s + 1]; e += 32) {
+              const int lp = pl[tb.tt[e]];
+              const int nl = ls + lp + 1;
               const int u = tb.tu[e];
-              if (nl <= tb.K && nl < lev[u]) lev[u] = (unsigned char)nl;
+              if (lp <= K && nl <= K && nl < rl[u]) rl[u] = (unsigned char)nl;
             }
+            __syncwarp();
           }
         }
         // numeric pass (a pivot's dropped entries hold 0, so every pair may update)
         for (int s = 0; s < dg; ++s) {
-          if (lev[s] > tb.K) continue;
+          if (rl[s] > K) continue;
           const int sc = tb.slot[5 * (b + s) + 4];
           const int qp = ip[gp_col_lex(bx, tb.slot + 5 * (b + s), kx, ky, kz, kt)];
-          T* own_s = Fb + (long long)(b + s) * P + q;
-          const T l = *own_s * Fb[(long long)(tb.base[sc] + tb.diag[sc]) * P + qp];
-          *own_s = l;
-          for (int e = tb.tptr[b + s]; e < tb.tptr[b + s + 1]; ++e) {
+          const T* pv = F + g.foff + (long long)qp * tb.S;
+          const T l = rv[s] * pv[tb.base[sc] + tb.diag[sc]];
+          for (int e = tb.tptr[b + s] + lane; e < tb.tptr[b + s + 1]; e += 32) {
             const int u = tb.tu[e];
-            if (lev[u] > tb.K) continue;
-            Fb[(long long)(b + u) * P + q] -= l * Fb[(long long)tb.tt[e] * P + qp];
+            if (rl[u] <= K) rv[u] -= l * pv[tb.tt[e]];
           }
+          __syncwarp();
+          if (lane == 0) rv[s] = l;
         }
-        for (int u = 0; u < nrow; ++u) Lb[(b + u) * P + q] = lev[u] <= tb.K ? lev[u] : 255;
-        T* own_d = Fb + (long long)(b + dg) * P + q;
-        const T d = *own_d;
-        gp_check_pivot((double)d, status);
-        *own_d = (T)1 / d;
+        __syncwarp();
+        if (lane == 0) {
+          const T d = rv[dg];
+          gp_check_pivot((double)d, status);
+          rv[dg] = (T)1 / d;
+        }
+        __syncwarp();
+        for (int u = lane; u < nrow; u += 32) {
+          own[b + u] = rv[u];
+          ownl[b + u] = rl[u] <= K ? rl[u] : 255;
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -342,10 +369,11 @@ __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restric
 
 // z = sum over boxes (R^0)^T M^{-1} R^delta r with the pattern-driven factors:
 // one CTA per box gathers its residual, sweeps forward and backward by
-// wavefront (a kept entry is nonzero only inside the box; dropped entries
-// hold 0 and are skipped) and writes its owned points.
+// wavefront, one warp per point and row, its lanes summing over the slots (a
+// kept entry is nonzero only inside the box; dropped entries hold 0 and are
+// skipped), and writes its owned points.
 template <typename T>
-__global__ void __launch_bounds__(kGpThreads) gp_solve(const DevProblem* __restrict__ probs,
+__global__ void __launch_bounds__(kGpSolveThreads) gp_solve(const DevProblem* __restrict__ probs,
                                                        const BoxDesc* __restrict__ boxes, const GpBox* __restrict__ gb,
                                                        const int* __restrict__ perm, const int* __restrict__ iperm,
                                                        const int* __restrict__ lptr, GpTables tb,
@@ -356,10 +384,9 @@ __global__ void __launch_bounds__(kGpThreads) gp_solve(const DevProblem* __restr
   const BoxDesc bx = boxes[blockIdx.x];
   const GpBox g = gb[blockIdx.x];
   const DevProblem p = probs[bx.prob];
-  const T* Fb = F + g.foff;
   T* Vb = V + g.voff;
   const int* ip = iperm + g.poff;
-  const long long P = g.P;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x / 32;
   auto global_point = [&](int lex) {
     const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
     const int kt = lex / (bx.lx * bx.ly * bx.lz);
@@ -374,23 +401,29 @@ __global__ void __launch_bounds__(kGpThreads) gp_solve(const DevProblem* __restr
     for (int wi = 0; wi < g.nlev; ++wi) {
       const int w = pass == 0 ? wi : g.nlev - 1 - wi;
       const int l0 = lptr[g.loff + w], l1 = lptr[g.loff + w + 1];
-      for (int q = l0 + threadIdx.x; q < l1; q += blockDim.x) {
+      for (int q = l0 + wp; q < l1; q += kGpSolveThreads / 32) {
         const int lex = perm[g.poff + q];
         const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
         const int kt = lex / (bx.lx * bx.ly * bx.lz);
+        const T* Fp = F + g.foff + (long long)q * tb.S;
         for (int ci = 0; ci < 3; ++ci) {
           const int c = pass == 0 ? ci : 2 - ci;
           const int b = tb.base[c], dg = tb.diag[c];
           const int s0 = pass == 0 ? 0 : dg + 1, s1 = pass == 0 ? dg : tb.cnt[c];
-          T acc = Vb[3 * q + c];
-          for (int s = s0; s < s1; ++s) {
-            const T v = Fb[(long long)(b + s) * P + q];
+          T part = (T)0;
+          for (int s = s0 + lane; s < s1; s += 32) {
+            const T v = Fp[b + s];
             if (v == (T)0) continue;
             const signed char* sl = tb.slot + 5 * (b + s);
-            acc -= v * Vb[3 * ip[gp_col_lex(bx, sl, kx, ky, kz, kt)] + sl[4]];
+            part += v * Vb[3 * ip[gp_col_lex(bx, sl, kx, ky, kz, kt)] + sl[4]];
           }
-          if (pass == 1) acc *= Fb[(long long)(b + dg) * P + q];   // the stored 1 / u_ii
-          Vb[3 * q + c] = acc;
+          for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          if (lane == 0) {
+            T acc = Vb[3 * q + c] - part;
+            if (pass == 1) acc *= Fp[b + dg];   // the stored 1 / u_ii
+            Vb[3 * q + c] = acc;
+          }
+          __syncwarp();
         }
       }
       __syncthreads();
@@ -414,8 +447,8 @@ kkt_status gp_factor_t(ras_precond* m, cudaStream_t s) {
   GpFactor* f = m->gp;
   int pmax = 0;
   for (const GpBox& b : f->boxes_h) pmax = std::max(pmax, b.P);
-  gp_gather<T><<<dim3((pmax + 127) / 128, m->nbox), 128, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->tab,
-                                                                 (T*)f->F, f->LV);
+  gp_gather<T><<<dim3((pmax + 7) / 8, m->nbox), 256, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->tab,
+                                                             (T*)f->F, f->LV);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
   {
@@ -437,10 +470,10 @@ kkt_status gp_factor(ras_precond* m, cudaStream_t s) {
 kkt_status gp_solve(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate) {
   GpFactor* f = m->gp;
   if (f->prec == 64)
-    gp_solve<double><<<m->nbox, kGpThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab,
+    gp_solve<double><<<m->nbox, kGpSolveThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab,
                                                     (const double*)f->F, (double*)f->V, r, z, gate);
   else
-    gp_solve<float><<<m->nbox, kGpThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab,
+    gp_solve<float><<<m->nbox, kGpSolveThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab,
                                                    (const float*)f->F, (float*)f->V, r, z, gate);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
