@@ -176,3 +176,55 @@ def test_p1_two_level_solve_matches_direct_solve(api, prec):
     f = prob.recover_source(x).cpu().numpy()
     fr = okkt.source(p, U)
     assert np.linalg.norm(f - fr) <= 1e-5 * np.linalg.norm(fr)
+
+
+# ---------------------------------------------------------------------------
+# benchmark size (32^3 cells x 64 steps, 7.0M unknowns) under P1
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def mid_p1(api):
+    w = dataclasses.replace(W.mid(), element="p1")
+    return w, okkt.Problem.from_workload(w), api.Problem.from_workload(w)
+
+
+def test_p1_matvec_full_size_matches_levelwise_oracle(api, mid_p1):
+    from test_gpu_kkt import _abs_bound   # (|F| |x|)_i from the block rows
+
+    w, p, prob = mid_p1
+    x = W.random_vector(prob.n, 22)
+    y = prob.apply(_dev(x)).cpu().numpy()
+    assert np.all(np.abs(y - okkt.apply(p, x)) <= 1e-12 * _abs_bound(p, x))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_p1_fine_ras_full_size_interior_box_matches_oracle(api, mid_p1, prec):
+    # the instance the benchmark's P1 form runs (local vectors in global memory, 4 lanes)
+    w, p, prob = mid_p1
+    r = W.random_vector(prob.n, 23)
+    bxs = osch.boxes(p, w.nsub, w.overlap)
+    bi = 1 + w.nsub[0] * (1 + w.nsub[1] * (1 + w.nsub[2] * 1))
+    nodes, levels = osch.box_nodes_levels(p, bxs[bi])
+    idx, owned = osch.box_unknowns(p, bxs[bi])
+    zr = osch.ILU0(okkt.assemble_box(p, nodes, levels), osch.local_pattern(p, idx)).solve(r[idx])[owned]
+    ras = api.RAS(prob, w.nsub, w.overlap, prec)
+    sh = ras.solve_shape()
+    assert not sh["smem_vectors"] and sh["lanes"] == 4
+    z = ras.apply(_dev(r)).cpu().numpy()[idx[owned]]
+    if prec == 64:
+        assert np.abs(z - zr).max() <= 1e-9 * np.abs(zr).max()
+    else:
+        assert np.linalg.norm(z - zr) <= 1e-3 * np.linalg.norm(zr)
+
+
+def test_p1_mixed_solve_full_size_true_residual(api, mid_p1):
+    w, p, prob = mid_p1
+    rng = np.random.default_rng(24)
+    cobs = rng.standard_normal((w.M + 1, len(w.sensor_xyz)))
+    ras = api.RAS(prob, w.nsub, w.overlap, 32)
+    co = api.Coarse(prob, w.coarse_cells, w.coarse_M, w.nsub, w.coarse_overlap, w.coarse_rtol, w.coarse_maxit, 32)
+    b = prob.rhs(_dev(cobs))
+    x, st, its, rel = api.gmres_solve(prob, b, ras=ras, coarse=co, restart=w.restart, rtol=1e-8, maxit=2000)
+    assert st == 0
+    bo = okkt.rhs(p, cobs)
+    assert np.linalg.norm(bo - okkt.apply(p, x.cpu().numpy())) <= 1e-8 * np.linalg.norm(bo)
