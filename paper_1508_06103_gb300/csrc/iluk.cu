@@ -35,6 +35,7 @@
 #include <array>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "ras.cuh"
@@ -135,6 +136,8 @@ std::array<std::vector<GpSlot>, 3> block_rows() {
 std::array<std::vector<GpSlot>, 3> gp_rows(int local) {
   static std::array<std::vector<GpSlot>, 3> ilu1, blk;   // built once per process
   static bool have1 = false, haveb = false;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
   if (local == 2) {
     if (!have1) {
       ilu1 = ilu1_interior_rows();
