@@ -467,14 +467,33 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
     const S* B = buf0 + (size_t)b * bstride;
     T sc = 0, sg = 0, sf = 0;
     if constexpr (!kUpper) {
+      if constexpr (sizeof(T) == 8) {
+        // FP64: one FMA per product into two chains per sum (the FP64 pipe
+        // is the limit: a product pair costs 2 operations instead of 3)
+        T sc1 = 0, sf1 = 0;
 #pragma unroll
-      for (int i = 0; i < kNbrPerLane; ++i) {
-        const int q = lane + kLanes * i;
-        const S* rc = B + (2 * q) * cp + j;
-        const S* rf = B + (94 + 2 * q) * cp + j;
-        sc += arith<T>(rc[0]) * nc[i] + arith<T>(rc[cp]) * nf[i];
-        sf += arith<T>(rf[0]) * ng[i] + arith<T>(rf[cp]) * nf[i];
-        if (q >= 27) sg += arith<T>(B[(80 + q - 27) * cp + j]) * ng[i];
+        for (int i = 0; i < kNbrPerLane; ++i) {
+          const int q = lane + kLanes * i;
+          const S* rc = B + (2 * q) * cp + j;
+          const S* rf = B + (94 + 2 * q) * cp + j;
+          sc = fma(arith<T>(rc[0]), nc[i], sc);
+          sc1 = fma(arith<T>(rc[cp]), nf[i], sc1);
+          sf = fma(arith<T>(rf[0]), ng[i], sf);
+          sf1 = fma(arith<T>(rf[cp]), nf[i], sf1);
+          if (q >= 27) sg = fma(arith<T>(B[(80 + q - 27) * cp + j]), ng[i], sg);
+        }
+        sc += sc1;
+        sf += sf1;
+      } else {
+#pragma unroll
+        for (int i = 0; i < kNbrPerLane; ++i) {
+          const int q = lane + kLanes * i;
+          const S* rc = B + (2 * q) * cp + j;
+          const S* rf = B + (94 + 2 * q) * cp + j;
+          sc += arith<T>(rc[0]) * nc[i] + arith<T>(rc[cp]) * nf[i];
+          sf += arith<T>(rf[0]) * ng[i] + arith<T>(rf[cp]) * nf[i];
+          if (q >= 27) sg += arith<T>(B[(80 + q - 27) * cp + j]) * ng[i];
+        }
       }
       sc = lane_sum(sc);
       sg = lane_sum(sg);
@@ -488,14 +507,23 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
         st3(vp, yc, yg, yf);
       }
     } else {
+      T sf1 = 0;   // FP64: the f-row products in two FMA chains
 #pragma unroll
       for (int i = 0; i < kNbrPerLane; ++i) {
         const int q = lane + kLanes * i;
         const S* rf = B + (71 + 2 * q) * cp + j;
-        sf += arith<T>(rf[0]) * ng[i] + arith<T>(rf[cp]) * nf[i];
+        if constexpr (sizeof(T) == 8) {
+          sf = fma(arith<T>(rf[0]), ng[i], sf);
+          sf1 = fma(arith<T>(rf[cp]), nf[i], sf1);
+        } else {
+          sf += arith<T>(rf[0]) * ng[i] + arith<T>(rf[cp]) * nf[i];
+        }
         if (q < 13) {
           const S* rc = B + (2 + 2 * q) * cp + j;
-          sc += arith<T>(rc[0]) * nc[i] + arith<T>(rc[cp]) * nf[i];
+          if constexpr (sizeof(T) == 8)
+            sc = fma(arith<T>(rc[cp]), nf[i], fma(arith<T>(rc[0]), nc[i], sc));
+          else
+            sc += arith<T>(rc[0]) * nc[i] + arith<T>(rc[cp]) * nf[i];
           sg += arith<T>(B[(29 + q) * cp + j]) * ng[i];
         } else {
           const int d = q - 13;
@@ -503,6 +531,7 @@ __global__ void __launch_bounds__(solve_threads_max<S>(), 2) ras_solve(
           if (d == 13) sg += arith<T>(B[55 * cp + j]) * nc[i];
         }
       }
+      sf += sf1;
       sc = lane_sum(sc);
       sg = lane_sum(sg);
       sf = lane_sum(sf);
