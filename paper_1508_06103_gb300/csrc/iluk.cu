@@ -12,10 +12,12 @@
 // {-1, 0, 1}^4.  A point near a box face or the domain boundary uses a subset:
 // the per-point levels decide which slots it keeps.
 //
-// Values and levels.  Point-major per box: slot s of the point in schedule
-// position q at F[foff + q * S + s] (a warp takes one point, its lanes
-// consecutive slots), its level of fill at LV[...] (0 for an entry of F_h's
-// structural pattern, 255 for a slot the point does not have).
+// Values and levels.  Point-major per box, by the point's lexicographic index
+// in the box (so a column's address is arithmetic on the point's, with no
+// index lookup): slot s of point lex at F[foff + lex * S + s] (a warp takes
+// one point, its lanes consecutive slots), its level of fill at LV[...] (0 for
+// an entry of F_h's structural pattern, 255 for a slot the point does not
+// have).  The local vectors of the solve are indexed the same way.
 //
 // Elimination (IKJ, rows in the natural point-block order, as the oracle's
 // ILU0 on the same pattern).  For row (p, c): a symbolic pass over the L slots
@@ -176,9 +178,9 @@ extern "C" kkt_status ras_local_pattern(int local, int counts[3]) {
 
 // Per-box storage of the pattern-driven factors.
 struct GpBox {
-  long long foff;   // values / levels: slot s of schedule position q at foff + q * S + s
+  long long foff;   // values / levels: slot s of point lex (box-lexicographic) at foff + lex * S + s
   long long voff;   // local vector: 3 values per point
-  long long poff;   // schedule arrays (perm, iperm)
+  long long poff;   // schedule array (perm: schedule position -> lexicographic index)
   long long loff;   // wavefront pointers
   int nlev;
   int P;
@@ -202,7 +204,6 @@ struct GpFactor {
   std::vector<GpBox> boxes_h;
   GpBox* boxes = nullptr;
   int* perm = nullptr;
-  int* iperm = nullptr;
   int* lptr = nullptr;
   signed char* slot = nullptr;
   short* smap = nullptr;
@@ -216,7 +217,6 @@ struct GpFactor {
   ~GpFactor() {
     cudaFree(boxes);
     cudaFree(perm);
-    cudaFree(iperm);
     cudaFree(lptr);
     cudaFree(slot);
     cudaFree(smap);
@@ -259,9 +259,10 @@ __global__ void gp_gather(const DevProblem* __restrict__ probs, const BoxDesc* _
   if (q >= g.P) return;
   const DevProblem p = probs[bx.prob];
   const Coefs<T> cf = coefs<T>(p);
-  const PointRow<T> pr = point_row<T>(p, bx, perm[g.poff + q]);
+  const int lex = perm[g.poff + q];
+  const PointRow<T> pr = point_row<T>(p, bx, lex);
   const bool idC = pr.n == 0 || pr.dirj, idG = pr.n == p.M || pr.dirj;
-  const long long o = g.foff + (long long)q * tb.S;
+  const long long o = g.foff + (long long)lex * tb.S;
   for (int s = lane; s < tb.S; s += 32) {
     const signed char* sl = tb.slot + 5 * s;
     const int c = gp_row_of(tb, s);
@@ -296,14 +297,13 @@ constexpr int kGpWarps = kGpThreads / 32;
 template <typename T>
 __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restrict__ boxes,
                                                         const GpBox* __restrict__ gb, const int* __restrict__ perm,
-                                                        const int* __restrict__ iperm, const int* __restrict__ lptr,
+                                                        const int* __restrict__ lptr,
                                                         GpTables tb, T* __restrict__ F, unsigned char* __restrict__ LV,
                                                         int* __restrict__ status) {
   __shared__ T rowv[kGpWarps][kGpMaxRow];
   __shared__ unsigned char rowl[kGpWarps][kGpMaxRow];
   const BoxDesc bx = boxes[blockIdx.x];
   const GpBox g = gb[blockIdx.x];
-  const int* ip = iperm + g.poff;
   const int lane = threadIdx.x & 31, wp = threadIdx.x / 32;
   T* rv = rowv[wp];
   unsigned char* rl = rowl[wp];
@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restric
       const int lex = perm[g.poff + q];
       const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
       const int kt = lex / (bx.lx * bx.ly * bx.lz);
-      T* own = F + g.foff + (long long)q * tb.S;
-      unsigned char* ownl = LV + g.foff + (long long)q * tb.S;
+      T* own = F + g.foff + (long long)lex * tb.S;
+      unsigned char* ownl = LV + g.foff + (long long)lex * tb.S;
       for (int c = 0; c < 3; ++c) {
         const int b = tb.base[c], nrow = tb.cnt[c], dg = tb.diag[c];
         for (int u = lane; u < nrow; u += 32) {
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restric
           for (int s = 0; s < dg; ++s) {
             const int ls = rl[s];
             if (ls > K) continue;
-            const int qp = ip[gp_col_lex(bx, tb.slot + 5 * (b + s), kx, ky, kz, kt)];
+            const int qp = gp_col_lex(bx, tb.slot + 5 * (b + s), kx, ky, kz, kt);
             const unsigned char* pl = LV + g.foff + (long long)qp * tb.S;
             for (int e = tb.tptr[b + s] + lane; e < tb.tptr[b + s + 1]; e += 32) {
               const int lp = pl[tb.tt[e]];
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restric
         for (int s = 0; s < dg; ++s) {
           if (rl[s] > K) continue;
           const int sc = tb.slot[5 * (b + s) + 4];
-          const int qp = ip[gp_col_lex(bx, tb.slot + 5 * (b + s), kx, ky, kz, kt)];
+          const int qp = gp_col_lex(bx, tb.slot + 5 * (b + s), kx, ky, kz, kt);
           const T* pv = F + g.foff + (long long)qp * tb.S;
           const T l = rv[s] * pv[tb.base[sc] + tb.diag[sc]];
           for (int e = tb.tptr[b + s] + lane; e < tb.tptr[b + s + 1]; e += 32) {
@@ -372,13 +372,13 @@ __global__ void __launch_bounds__(kGpThreads) gp_factor(const BoxDesc* __restric
 
 // z = sum over boxes (R^0)^T M^{-1} R^delta r with the pattern-driven factors:
 // one CTA per box gathers its residual, sweeps forward and backward by
-// wavefront, one warp per point and row, its lanes summing over the slots (a
-// kept entry is nonzero only inside the box; dropped entries hold 0 and are
-// skipped), and writes its owned points.
+// wavefront, one warp per point and row, its lanes summing over the slots
+// (slots whose column leaves the box are skipped; dropped entries hold 0),
+// and writes its owned points.
 template <typename T>
 __global__ void __launch_bounds__(kGpSolveThreads) gp_solve(const DevProblem* __restrict__ probs,
                                                        const BoxDesc* __restrict__ boxes, const GpBox* __restrict__ gb,
-                                                       const int* __restrict__ perm, const int* __restrict__ iperm,
+                                                       const int* __restrict__ perm,
                                                        const int* __restrict__ lptr, GpTables tb,
                                                        const T* __restrict__ F, T* __restrict__ V,
                                                        const double* __restrict__ r, double* __restrict__ z,
@@ -388,16 +388,15 @@ __global__ void __launch_bounds__(kGpSolveThreads) gp_solve(const DevProblem* __
   const GpBox g = gb[blockIdx.x];
   const DevProblem p = probs[bx.prob];
   T* Vb = V + g.voff;
-  const int* ip = iperm + g.poff;
   const int lane = threadIdx.x & 31, wp = threadIdx.x / 32;
   auto global_point = [&](int lex) {
     const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
     const int kt = lex / (bx.lx * bx.ly * bx.lz);
     return (long long)(bx.t0 + kt) * p.N + (bx.x0 + kx) + (long long)p.nx * ((bx.y0 + ky) + (long long)p.ny * (bx.z0 + kz));
   };
-  for (int q = threadIdx.x; q < g.P; q += blockDim.x) {   // R^delta r
-    const long long gi = 3 * global_point(perm[g.poff + q]);
-    for (int c = 0; c < 3; ++c) Vb[3 * q + c] = (T)r[gi + c];
+  for (int lex = threadIdx.x; lex < g.P; lex += blockDim.x) {   // R^delta r
+    const long long gi = 3 * global_point(lex);
+    for (int c = 0; c < 3; ++c) Vb[3 * lex + c] = (T)r[gi + c];
   }
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
@@ -408,23 +407,25 @@ __global__ void __launch_bounds__(kGpSolveThreads) gp_solve(const DevProblem* __
         const int lex = perm[g.poff + q];
         const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
         const int kt = lex / (bx.lx * bx.ly * bx.lz);
-        const T* Fp = F + g.foff + (long long)q * tb.S;
+        const T* Fp = F + g.foff + (long long)lex * tb.S;
         for (int ci = 0; ci < 3; ++ci) {
           const int c = pass == 0 ? ci : 2 - ci;
           const int b = tb.base[c], dg = tb.diag[c];
           const int s0 = pass == 0 ? 0 : dg + 1, s1 = pass == 0 ? dg : tb.cnt[c];
           T part = (T)0;
+#pragma unroll 4
           for (int s = s0 + lane; s < s1; s += 32) {
-            const T v = Fp[b + s];
-            if (v == (T)0) continue;
+            // the column from the slot table alone, so the value and vector loads are independent
             const signed char* sl = tb.slot + 5 * (b + s);
-            part += v * Vb[3 * ip[gp_col_lex(bx, sl, kx, ky, kz, kt)] + sl[4]];
+            const int cl = gp_col_lex(bx, sl, kx, ky, kz, kt);
+            const T v = Fp[b + s];
+            if (cl >= 0) part += v * Vb[3 * cl + sl[4]];
           }
           for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
           if (lane == 0) {
-            T acc = Vb[3 * q + c] - part;
+            T acc = Vb[3 * lex + c] - part;
             if (pass == 1) acc *= Fp[b + dg];   // the stored 1 / u_ii
-            Vb[3 * q + c] = acc;
+            Vb[3 * lex + c] = acc;
           }
           __syncwarp();
         }
@@ -432,8 +433,7 @@ __global__ void __launch_bounds__(kGpSolveThreads) gp_solve(const DevProblem* __
       __syncthreads();
     }
   }
-  for (int q = threadIdx.x; q < g.P; q += blockDim.x) {   // (R^0)^T: owned points only
-    const int lex = perm[g.poff + q];
+  for (int lex = threadIdx.x; lex < g.P; lex += blockDim.x) {   // (R^0)^T: owned points only
     const int kx = lex % bx.lx, ky = (lex / bx.lx) % bx.ly, kz = (lex / (bx.lx * bx.ly)) % bx.lz;
     const int kt = lex / (bx.lx * bx.ly * bx.lz);
     const int x = bx.x0 + kx, y = bx.y0 + ky, zz = bx.z0 + kz, t = bx.t0 + kt;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kGpSolveThreads) gp_solve(const DevProblem* __
         t >= bx.ot1)
       continue;
     const long long gi = 3 * global_point(lex);
-    for (int c = 0; c < 3; ++c) z[gi + c] = (double)Vb[3 * q + c];
+    for (int c = 0; c < 3; ++c) z[gi + c] = (double)Vb[3 * lex + c];
   }
 }
 
@@ -456,7 +456,7 @@ kkt_status gp_factor_t(ras_precond* m, cudaStream_t s) {
   KKT_TRY_CUDA(cudaGetLastError());
   {
     TimedScope timed(&m->factor_timing, s);
-    gp_factor<T><<<m->nbox, kGpThreads, 0, s>>>(m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab, (T*)f->F,
+    gp_factor<T><<<m->nbox, kGpThreads, 0, s>>>(m->boxes, f->boxes, f->perm, f->lptr, f->tab, (T*)f->F,
                                                 f->LV, m->status);
   }
   KKT_COUNT(1);
@@ -473,10 +473,10 @@ kkt_status gp_factor(ras_precond* m, cudaStream_t s) {
 kkt_status gp_solve(ras_precond* m, const double* r, double* z, cudaStream_t s, const int* gate) {
   GpFactor* f = m->gp;
   if (f->prec == 64)
-    gp_solve<double><<<m->nbox, kGpSolveThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab,
+    gp_solve<double><<<m->nbox, kGpSolveThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->lptr, f->tab,
                                                     (const double*)f->F, (double*)f->V, r, z, gate);
   else
-    gp_solve<float><<<m->nbox, kGpSolveThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->iperm, f->lptr, f->tab,
+    gp_solve<float><<<m->nbox, kGpSolveThreads, 0, s>>>(m->dprobs, m->boxes, f->boxes, f->perm, f->lptr, f->tab,
                                                    (const float*)f->F, (float*)f->V, r, z, gate);
   KKT_COUNT(1);
   KKT_TRY_CUDA(cudaGetLastError());
@@ -587,7 +587,7 @@ kkt_status gp_create(ras_precond* m, int local, int prec) {
         return KKT_ERR_ARG;
       }
     }
-  std::vector<int> perm, iperm, lptr;
+  std::vector<int> perm, lptr;
   long long foff = 0, voff = 0;
   for (const BoxDesc& bx : m->boxes_h) {
     GpBox g{};
@@ -606,15 +606,13 @@ kkt_status gp_create(ras_precond* m, int local, int prec) {
     for (int lex = 0; lex < g.P; ++lex) cnt[wof(lex) + 1]++;
     for (int w = 0; w < g.nlev; ++w) cnt[w + 1] += cnt[w];
     for (int w = 0; w <= g.nlev; ++w) lptr.push_back(cnt[w]);
-    std::vector<int> pb(g.P), ib(g.P);
+    std::vector<int> pb(g.P);
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
     for (int lex = 0; lex < g.P; ++lex) {
       const int q = fill[wof(lex)]++;
       pb[q] = lex;
-      ib[lex] = q;
     }
     perm.insert(perm.end(), pb.begin(), pb.end());
-    iperm.insert(iperm.end(), ib.begin(), ib.end());
     f->boxes_h.push_back(g);
     foff += (long long)tb.S * g.P;
     voff += 3LL * g.P;
@@ -634,7 +632,6 @@ kkt_status gp_create(ras_precond* m, int local, int prec) {
   };
   KKT_TRY(up(&f->boxes, f->boxes_h));
   KKT_TRY(up(&f->perm, perm));
-  KKT_TRY(up(&f->iperm, iperm));
   KKT_TRY(up(&f->lptr, lptr));
   KKT_TRY(up(&f->slot, slot));
   KKT_TRY(up(&f->smap, smap));
