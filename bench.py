@@ -560,6 +560,9 @@ def kernel_arm(args):
             tf = [api.fma_peak(prec)[0] for _ in range(5)]
             res[f"fp{prec}_fma_tflops"] = max(tf)
             res[f"fp{prec}_fma_tflops_runs"] = tf
+        tm = [api.mma_peak()[0] for _ in range(5)]
+        res["fp64_mma_tflops"] = max(tm)
+        res["fp64_mma_tflops_runs"] = tm
         print(json.dumps({"kernel": "peaks", **res}))
         return
     if args.kernel == "ras":

@@ -461,6 +461,16 @@ kkt_status kkt_timing_reset(kkt_problem* p, ras_precond* m);
 kkt_status kkt_fma_peak(int precision, double* tflops, double* ms, void* stream);
 
 /*
+ * kkt_mma_peak -- measured FP64 tensor-core rate of the current device: every
+ *   warp runs 8 independent chains of the m8n8k4 FP64 warp-level
+ *   matrix multiply-accumulate (512 flops per instruction) on register
+ *   operands; CUDA events on `stream`.  Instrumentation beside kkt_fma_peak (it
+ *   decides whether FP64 MMA could beat the FP64 FMA pipe on dense panels).
+ *   tflops (host) required, ms (host) optional.  Errors: ARG, CUDA.
+ */
+kkt_status kkt_mma_peak(double* tflops, double* ms, void* stream);
+
+/*
  * recover_source -- f of the point-block vector U as an (M+1) x N array
  *   (Sec. 3.2 ordering; the recovered source of the inverse problem).
  */

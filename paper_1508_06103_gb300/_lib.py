@@ -69,6 +69,7 @@ SIGNATURES = {
     "two_level_refactor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "kkt_launch_count": (C.c_longlong, []),
     "kkt_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
+    "kkt_mma_peak": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "kkt_timing_enable": (C.c_int, [C.c_int]),
     "kkt_timing_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "ras_timing_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),

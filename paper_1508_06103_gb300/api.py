@@ -245,6 +245,13 @@ def fma_peak(precision: int = 64, stream=None):
     return tf.value, ms.value
 
 
+def mma_peak(stream=None):
+    """(TFLOP/s, ms) of the device's FP64 tensor-core (MMA) rate (kkt_mma_peak)."""
+    tf, ms = C.c_double(), C.c_double()
+    check(_lib.load().kkt_mma_peak(C.byref(tf), C.byref(ms), _stream(stream)), "kkt_mma_peak")
+    return tf.value, ms.value
+
+
 def timing_enable(on: bool) -> bool:
     return bool(_lib.load().kkt_timing_enable(int(on)))
 

@@ -1,6 +1,7 @@
-// FMA throughput of the device in FP64 and FP32 (instrumentation: the
-// denominators of the FP64 KKT matvec's pipe fraction; the paper has no
-// counterpart).  Every thread runs 8 independent multiply-add chains
+// FMA throughput of the device in FP64 and FP32, and its FP64 tensor-core
+// (MMA) rate (instrumentation: the denominators of the FP64 KKT matvec's pipe
+// fraction, and the check of whether FP64 MMA could serve the dense panels;
+// the paper has no counterpart).  Every thread runs 8 independent multiply-add chains
 // x <- x a + b for `iters` rounds, all in registers, so the count of
 // multiply-adds is exact and nothing else limits the rate; the time is
 // taken with CUDA events on the given stream.
@@ -44,7 +45,67 @@ kkt_status run(int iters, int blocks, T* out, cudaStream_t s, float* ms) {
   return KKT_OK;
 }
 
+// FP64 matrix multiply-accumulate: every warp runs kChains independent chains
+// D <- A B + D of the m8n8k4 FP64 warp-level MMA (512 flops per instruction
+// and warp), operands in registers.
+__global__ void __launch_bounds__(kPeakThreads) dmma_chains(double* __restrict__ out, int iters) {
+  const double a = 1.0 + 1e-6 * threadIdx.x, b = 1e-3;
+  double d0[kChains], d1[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) d0[c] = d1[c] = (double)c;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(d0[c]), "+d"(d1[c])
+                   : "d"(a), "d"(b));
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += d0[c] + d1[c];
+  if (s == -1.0) out[blockIdx.x] = s;   // never true: keeps the chains live
+}
+
 }  // namespace
+
+// FP64 tensor-core (MMA) rate of the current device; see stkkt.h.
+extern "C" kkt_status kkt_mma_peak(double* tflops, double* ms, void* stream) {
+  if (!tflops) {
+    set_error("kkt_mma_peak: a tflops output is required");
+    return KKT_ERR_ARG;
+  }
+  int dev = 0, nsm = 0;
+  KKT_TRY_CUDA(cudaGetDevice(&dev));
+  KKT_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = nsm * 8, iters = 1024;
+  double* out = nullptr;
+  KKT_TRY_CUDA(cudaMalloc(&out, blocks * sizeof(double)));
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  float t = 0.f;
+  kkt_status st = KKT_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = KKT_ERR_CUDA;
+  if (st == KKT_OK) {
+    dmma_chains<<<blocks, kPeakThreads, 0, s>>>(out, iters);   // warm-up
+    cudaEventRecord(e0, s);
+    dmma_chains<<<blocks, kPeakThreads, 0, s>>>(out, iters);
+    cudaEventRecord(e1, s);
+    KKT_COUNT(2);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+      st = KKT_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaFree(out);
+  if (st != KKT_OK) {
+    set_error("kkt_mma_peak: CUDA error");
+    return st;
+  }
+  const double flops = 512.0 * kChains * (double)iters * (kPeakThreads / 32) * blocks;
+  *tflops = flops / (t * 1e-3) / 1e12;
+  if (ms) *ms = t;
+  return KKT_OK;
+}
 
 extern "C" kkt_status kkt_fma_peak(int precision, double* tflops, double* ms, void* stream) {
   if ((precision != 64 && precision != 32) || !tflops) {

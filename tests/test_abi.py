@@ -73,6 +73,7 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
     assert b"kkt_set_regularization" in lib.kkt_last_error()
     assert lib.reduced_solve(None, None, None, None, 30, 1e-8, 10, 1e-12, None, None, None, None) == -1
     assert b"reduced_solve" in lib.kkt_last_error()
+    assert lib.kkt_mma_peak(None, None, None) == -1
     assert lib.ras_local_pattern(2, None) == -1
     assert lib.ras_local_pattern(1, (ctypes.c_int * 3)()) == -1   # exact LU has no slot pattern
     assert lib.kkt_set_element(None, 1) == -1
