@@ -39,7 +39,8 @@ __device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
 
 // ---------------------------------------------------------------------------
 // Tiled matvec: one CTA owns a TX x TY x TZ tile of nodes and a run of NT time
-// levels; one thread per output node.  Per level the six time combinations
+// levels (NT = levels_per_cta<T>(): 4 in FP64, 8 in FP32); one thread per
+// output node.  Per level the six time combinations
 //   u1 = (C^n - C^{n-1}) - tau (theta f^n + (1-theta) f^{n-1})   (C row, via B)
 //   u2 = tau (theta C^n + (1-theta) C^{n-1})                        (C row, via S)
 //   u3 = G^n - G^{n+1}                                              (G row, via B)
@@ -63,7 +64,14 @@ __device__ __forceinline__ Coefs<float> coefs<float>(const DevProblem& p) {
 // covers grids of 11 k nodes per axis without ragged tiles (33^3 and 65^3
 // nodes: 40 x 40 x 36 / 33^3 = 1.6x the nodes with 8 x 8 x 4 tiles); the host
 // picks the shape with the least estimated work (launch_tiled).
-constexpr int NT = 16;   // levels per CTA
+// Levels per CTA: shorter runs give more CTAs for the same work (two halo
+// levels more per run).  Measured at 32^3 x 64 with the inputs out of L2
+// (runs of 16 / 8 / 4 levels): FP64 1.127 / 1.047 / 1.018 ms, FP32 0.158 /
+// 0.153 / 0.159 ms.
+template <typename T>
+__host__ __device__ constexpr int levels_per_cta() {
+  return sizeof(T) == 8 ? 4 : 8;
+}
 template <int TX_, int TY_, int TZ_>
 struct Tile {
   static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
@@ -189,6 +197,7 @@ __global__ void __launch_bounds__(Tl::kThreads) matvec_tiled(DevProblem p, const
   const int N = p.N, M = p.M;
   const int tile = blockIdx.x;
   const int bx0 = (tile % tiles_x) * TX, by0 = ((tile / tiles_x) % tiles_y) * TY, bz0 = (tile / (tiles_x * tiles_y)) * TZ;
+  constexpr int NT = levels_per_cta<T>();
   const int n0 = blockIdx.y * NT, n1 = min(n0 + NT, M + 1);
   const Coefs<T> c = coefs<T>(p);
   const T tau = (T)p.tau, th = (T)p.theta, th1 = (T)(1.0 - p.theta);
@@ -392,6 +401,7 @@ double tile_work(const DevProblem& p) {
 template <typename T, typename Tl, bool kP1 = false>
 void launch_shape(const DevProblem& p, const T* x, T* y, const double* b, cudaStream_t s) {
   const int tx = (p.nx + Tl::TX - 1) / Tl::TX, ty = (p.ny + Tl::TY - 1) / Tl::TY, tz = (p.nz + Tl::TZ - 1) / Tl::TZ;
+  constexpr int NT = levels_per_cta<T>();
   dim3 grid(tx * ty * tz, (p.M + 1 + NT - 1) / NT);
   Axis1D<T> ax, ay, az;
   ax.init(p.nx, p.hx);
