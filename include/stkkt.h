@@ -190,7 +190,7 @@ kkt_status ras_local_pattern(int local, int counts[3]);
  *                blocks of the 81-point neighbourhood (Sec. 3.2 point-block
  *                ordering; diagonal blocks factored exactly).  2 and 3: FP64
  *                or FP32 (factor_prec 64 or 32), one problem, factor values
- *                stored rank-major per box (ras_local_pattern slots per row),
+ *                stored point-major per box (ras_local_pattern slots per row),
  *                no static apply; their solve runs one CTA per box with a
  *                barrier per wavefront.
  *   factor_prec  64 = factor and solve in FP64, 32 = FP32, 16 = factor in FP32
