@@ -11,6 +11,32 @@
 
 #include "stkkt.h"
 
+// NVTX ranges around the library's host entry points (tracing under a
+// profiler; no-ops without one attached): the header-only NVTX 3 C API of
+// the CUDA toolkit, left out where the toolkit has no such header.
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define KKT_HAVE_NVTX 1
+#endif
+#endif
+struct NvtxRange {
+  explicit NvtxRange(const char* name) {
+#ifdef KKT_HAVE_NVTX
+    nvtxRangePushA(name);
+#else
+    (void)name;
+#endif
+  }
+  ~NvtxRange() {
+#ifdef KKT_HAVE_NVTX
+    nvtxRangePop();
+#endif
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void set_error(const std::string& msg);
 
 #define KKT_TRY_CUDA(call)                                                        \

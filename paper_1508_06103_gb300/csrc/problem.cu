@@ -442,6 +442,7 @@ kkt_status create_problem(const kkt_grid* g, int nt, double dt, const double* a_
 extern "C" kkt_status kkt_create(const kkt_grid* g, int nt, double dt, const double* a_cell, const double* v_cell,
                                  const int* sensor_node, int nsens, double beta1, double beta2, double theta,
                                  kkt_problem** out) {
+  NvtxRange nvtx_("kkt_create");
   return create_problem(g, nt, dt, a_cell, v_cell, sensor_node, nsens, beta1, beta2, theta, out);
 }
 

@@ -1122,6 +1122,7 @@ kkt_status ras_check(ras_precond* m) {
 
 extern "C" kkt_status ras_setup(kkt_problem* p, const int nsub[4], int overlap, int local, int factor_prec,
                                 ras_precond** out) {
+  NvtxRange nvtx_("ras_setup");
   return ras_create(&p, 1, nsub, overlap, local, factor_prec, nullptr, out);
 }
 
@@ -1152,6 +1153,7 @@ extern "C" kkt_status ras_setup_batch(kkt_problem* const* probs, int nprob, cons
 }
 
 extern "C" kkt_status ras_apply(ras_precond* m, const double* r, double* z, void* stream) {
+  NvtxRange nvtx_("ras_apply");
   if (!m || !r || !z) {
     set_error("ras_apply: null argument");
     return KKT_ERR_ARG;
@@ -1224,6 +1226,7 @@ extern "C" kkt_status ras_info(const ras_precond* m, int* nbox, long long* point
 }
 
 extern "C" kkt_status ras_refactor(ras_precond* m, void* stream) {
+  NvtxRange nvtx_("ras_refactor");
   if (!m) {
     set_error("ras_refactor: null argument");
     return KKT_ERR_ARG;

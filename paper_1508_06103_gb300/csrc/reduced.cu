@@ -565,6 +565,7 @@ struct HessOp : Operator {   // H f = W f - D G_lin(C_lin(f)): one forward and o
 extern "C" kkt_status reduced_solve(kkt_problem* p, const double* c_obs, const double* c0, double* U, int restart,
                                     double rtol, int maxit, double step_rtol, int* iters, double* relres,
                                     long long stats[4], void* stream) {
+  NvtxRange nvtx_("reduced_solve");
   if (!p || !U || (p->nsens > 0 && !c_obs) || restart < 1 || maxit < 1 || !(rtol > 0) || !(step_rtol > 0)) {
     set_error("reduced_solve: null argument, or restart, maxit, rtol or step_rtol not positive");
     return KKT_ERR_ARG;

@@ -225,6 +225,7 @@ struct TwoLevelOp : Operator {
 
 extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz, int cnt, const int nsub_c[4],
                                    int c_overlap, double c_rtol, int c_maxit, int factor_prec, coarse_level** out) {
+  NvtxRange nvtx_("coarse_setup");
   if (!fine || !nsub_c || !out) {
     set_error("coarse_setup: null argument");
     return KKT_ERR_ARG;
@@ -301,6 +302,7 @@ extern "C" kkt_status coarse_setup(kkt_problem* fine, int ccx, int ccy, int ccz,
 }
 
 extern "C" kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const double* x, double* z, void* stream) {
+  NvtxRange nvtx_("two_level_apply");
   if (!c || !fine || !x || !z || x == z) {
     set_error("two_level_apply: bad argument");
     return KKT_ERR_ARG;
@@ -313,6 +315,7 @@ extern "C" kkt_status two_level_apply(coarse_level* c, ras_precond* fine, const 
 }
 
 extern "C" kkt_status coarse_refactor(coarse_level* c, void* stream) {
+  NvtxRange nvtx_("coarse_refactor");
   if (!c) {
     set_error("coarse_refactor: null argument");
     return KKT_ERR_ARG;
@@ -365,6 +368,7 @@ extern "C" void coarse_destroy(coarse_level* c) {
 extern "C" kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* c, const double* b, double* x,
                                   int restart, double rtol, int maxit, int flexible, int* iters, double* true_relres,
                                   void* stream) {
+  NvtxRange nvtx_("gmres_solve");
   if (!p || !b || !x || b == x || restart < 1 || maxit < 0 || !(rtol > 0)) {
     set_error("gmres_solve: bad argument");
     return KKT_ERR_ARG;
@@ -400,6 +404,7 @@ extern "C" kkt_status gmres_solve(kkt_problem* p, ras_precond* m, coarse_level* 
 extern "C" kkt_status gmres_solve_batch(kkt_problem* const* probs, int nprob, ras_precond* m, const double* b,
                                         double* x, int restart, double rtol, int maxit, int* iters,
                                         double* true_relres, int* status, void* stream) {
+  NvtxRange nvtx_("gmres_solve_batch");
   if (!probs || nprob < 1 || !m || !b || !x || restart < 1 || maxit < 0 || !(rtol > 0)) {
     set_error("gmres_solve_batch: bad argument");
     return KKT_ERR_ARG;
