@@ -307,6 +307,25 @@ def reduced_solve(prob: Problem, c_obs: torch.Tensor, c0: Optional[torch.Tensor]
     return U, st, it.value, rel.value, dict(zip(names, list(stats)))
 
 
+def checkpoint_save(path: str, x: torch.Tensor, **meta) -> None:
+    """Write the iterate x of a solve (any device) and scalar metadata (iterations, residual,
+    ...) to an .npz file.  A restarted (F)GMRES starts every cycle from a fresh Krylov space, so
+    the iterate is the whole state: resuming is gmres_solve(prob, b, x=checkpoint_load(...)[0])."""
+    arrays = {"x": x.detach().cpu().numpy()}
+    for k, v in meta.items():
+        arrays["meta_" + k] = np.asarray(v)
+    with open(path, "wb") as fh:
+        np.savez(fh, **arrays)
+
+
+def checkpoint_load(path: str, device: str = "cuda"):
+    """(x on `device`, metadata dict) from checkpoint_save."""
+    with np.load(path) as z:
+        x = torch.from_numpy(z["x"].copy()).to(device)
+        meta = {k[5:]: z[k].item() if z[k].ndim == 0 else z[k] for k in z.files if k.startswith("meta_")}
+    return x, meta
+
+
 def _handles(probs: Sequence[Problem]):
     return (C.c_void_p * len(probs))(*[p.h.value for p in probs])
 
