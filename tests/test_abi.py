@@ -103,3 +103,23 @@ def test_local_patterns_of_an_interior_point():
     pat1 = schwarz.iluk_pattern(A, schwarz.local_pattern(p, idx), 1)
     centre = 2 + 5 * (2 + 5 * (2 + 5 * 2))
     assert api.local_pattern("ilu1") == [len(pat1[3 * centre + c]) for c in range(3)] == [780, 199, 667]
+
+
+def test_header_is_plain_c():
+    """include/stkkt.h is the C ABI: it compiles as C99 and as C++17 without warnings (the
+    exports themselves are checked against the header by the binding-coverage test)."""
+    import os
+    import shutil
+    import subprocess
+
+    import pytest
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = os.path.join(root, "include", "stkkt.h")
+    subprocess.run([cc, "-x", "c", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", hdr], check=True)
+    cxx = shutil.which("g++")
+    if cxx is not None:
+        subprocess.run([cxx, "-x", "c++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", hdr], check=True)
